@@ -1,0 +1,366 @@
+"""Benchmark: simulated images/s through the psfsim C ABI on one GB300 per rank.
+
+Workload (default): the 128 x 128 adjoint/fit configuration -- 40 synthetic
+Lyot PSFs of 128^2 at 0.25 lambda/D, a 128^2 scene, A = 16384 x 16384 FP32
+(1.07 GB, larger than L2, so no flush is needed between steps).  One step is
+one gradient evaluation of the ring fit's inner loop: the forward image
+S = A Z (Eq. 6) and the adjoint A^T g of an image-space residual, i.e. two
+full passes over A.  value = images simulated per second (one per step).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+column sample of the same workload (the paper's method has no GPU reference).
+Multi-GPU (torchrun) runs independent replicas: the path has no exchange step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "simulated images/s and GMAC/s (fraction of HBM/tensor roofline) vs plain FP32 GEMV at stated error"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    return rank, world, int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples taken during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        reasons = set()
+        for r in rows:
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                               r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def _workload():
+    from synth import workloads
+    w = workloads.adjoint_128()
+    lib32 = w.library().astype(np.float32)
+    x = workloads.random_ring_scene(w.N, w.S, w.r_max, w.seed + 5).ravel().astype(np.float32)
+    rng = np.random.default_rng(w.seed + 6)
+    g = rng.standard_normal(w.M).astype(np.float32)
+    return w, lib32, x, g
+
+
+def _gpu_arm(args, rank, world, local_rank):
+    import torch
+    from paper_2106_09122_gb300 import Plan
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w, lib32, x_np, g_np = _workload()
+    stream = torch.cuda.current_stream()
+    plan = Plan(torch.from_numpy(lib32).to(dev), w.radii, w.s, N=w.N, S=w.S)
+    x = torch.from_numpy(x_np).to(dev)
+    g = torch.from_numpy(g_np).to(dev)
+    y = torch.empty(w.M, dtype=torch.float32, device=dev)
+    gx = torch.empty(w.K, dtype=torch.float32, device=dev)
+    fscr = torch.empty(max(plan.forward_scratch_bytes(1), 1), dtype=torch.uint8, device=dev)
+    ascr = torch.empty(max(plan.adjoint_scratch_bytes(1), 1), dtype=torch.uint8, device=dev)
+
+    # build timing (one-off, context for the paper's Table 2)
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    plan2 = Plan(plan.lib, w.radii, w.s, N=w.N, S=w.S)
+    b1.record(stream)
+    torch.cuda.synchronize()
+    build_ms = b0.elapsed_time(b1)
+    del plan2
+
+    def step():
+        plan.forward(x, out=y, scratch=fscr)
+        plan.adjoint(g, out=gx, scratch=ascr)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    nsteps = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(nsteps):
+        ev[i][0].record(stream)
+        plan.forward(x, out=y, scratch=fscr)
+        ev[i][1].record(stream)
+        plan.adjoint(g, out=gx, scratch=ascr)
+        ev[i][2].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    fwd_ms = float(np.mean([a.elapsed_time(b) for a, b, _ in ev]))
+    adj_ms = float(np.mean([b.elapsed_time(c) for _, b, c in ev]))
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+
+    # e2e: host buffers through the same C-ABI calls, copies inside the timed region
+    hx = torch.from_numpy(x_np).pin_memory()
+    hg = torch.from_numpy(g_np).pin_memory()
+    hy = torch.empty(w.M, dtype=torch.float32).pin_memory()
+    hgx = torch.empty(w.K, dtype=torch.float32).pin_memory()
+    dx = torch.empty_like(x)
+    dg = torch.empty_like(g)
+
+    def e2e_step():
+        dx.copy_(hx, non_blocking=True)
+        dg.copy_(hg, non_blocking=True)
+        plan.forward(dx, out=y, scratch=fscr)
+        plan.adjoint(dg, out=gx, scratch=ascr)
+        hy.copy_(y, non_blocking=True)
+        hgx.copy_(gx, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(nsteps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # plain FP32 GEMV comparator (cuBLAS through torch) on the same stored A
+    A = plan.A_fp32()
+    for _ in range(3):
+        torch.mv(A, x)
+    torch.cuda.synchronize()
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    for _ in range(nsteps):
+        torch.mv(A, x)
+        torch.mv(A.t(), g)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    cmp_ms = c0.elapsed_time(c1) / nsteps
+    y_ref_cublas = torch.mv(A, x)
+    agree = float(((plan.forward(x) - y_ref_cublas).abs().max() / y_ref_cublas.abs().max()).item())
+
+    hbm, _, peak_kind = _peaks()
+    a_bytes = w.M * w.K * 4
+    fwd_bytes = a_bytes + w.K * 4 + w.M * 4
+    ms_per_step = elapsed_ms / nsteps
+    images = world * nsteps
+    out = {
+        "metric": METRIC,
+        "value": images / (elapsed_ms / 1e3),
+        "unit": "images/s",
+        "n_gpus": world,
+        "steps": nsteps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded Lyot-coronagraph PSFs, exozodi ring scene)",
+        "config": {"workload": f"{w.name}: n=N=128, s=S=0.25 lambda/D, 40 radii 0-12 lambda/D, "
+                               "A 16384x16384 FP32; step = forward A x + adjoint A^T g",
+                   "M": w.M, "K": w.K, "n_radii": len(w.radii), "storage": "fp32",
+                   "l2": "inputs larger than L2 (A is 1.07 GB), no flush",
+                   "parallelism": f"replicas x{world}"},
+        "gmac_per_s": images * 2 * w.M * w.K / (elapsed_ms / 1e3) / 1e9,
+        "kernels_ms": {"forward": fwd_ms, "adjoint": adj_ms, "build_once": build_ms},
+        "roofline": {"bound": "hbm", "achieved": fwd_bytes / (fwd_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": fwd_bytes / (fwd_ms / 1e3) / 1e9 / hbm, "traffic": None,
+                     "kernel": "psfsim forward (fwd_partial_kernel + fwd_reduce_kernel)",
+                     "peak_source": f"{peak_kind} hbm_gbs"},
+        "adjoint_roofline_frac": (a_bytes + w.K * 4 + w.M * 4) / (adj_ms / 1e3) / 1e9 / hbm,
+        "fp32_gemv_comparator": {"impl": "torch.mv (cuBLAS) forward + adjoint on the same A",
+                                 "ms_per_step": cmp_ms, "images_per_s": 1e3 / cmp_ms,
+                                 "max_rel_diff_vs_psfsim": agree},
+        "e2e": {"value": images / (e2e_ms / 1e3), "unit": "images/s",
+                "h2d_bytes_per_step": (w.K + w.M) * 4, "d2h_bytes_per_step": (w.M + w.K) * 4},
+        "gpu_launches": nsteps * 3,
+        "clocks": clk,
+    }
+    return out, plan, y, x_np, w, lib32
+
+
+def _oracle_sample(w, lib32, n_cols=512, seed=17):
+    """Column sample of the oracle's A (FP64) and the sampled column indices."""
+    from oracle import psfsim_oracle as O
+    rng = np.random.default_rng(seed)
+    cols = np.sort(rng.choice(w.K, n_cols, replace=False))
+    xs, ys = O.scene_offsets(w.N, w.S)
+    A_s = O.build_points(lib32.astype(np.float64), w.radii, xs[cols], ys[cols])
+    return cols, A_s
+
+
+def _oracle_step_time(w, A_s, cols, x_np, g_np, budget_s=10.0, max_steps=None):
+    """Seconds per full-size forward + adjoint step, extrapolated from the column sample."""
+    from oracle import psfsim_oracle as O
+    xs = x_np[cols].astype(np.float64)
+    g = g_np.astype(np.float64)
+    times = []
+    t_start = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        O.forward(A_s, xs)
+        O.adjoint(A_s, g)
+        times.append(time.perf_counter() - t0)
+        if (max_steps and len(times) >= max_steps) or (not max_steps and time.perf_counter() - t_start > budget_s):
+            break
+    per = float(np.median(times)) * w.K / len(cols)
+    return per, len(times)
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def _cpu_baseline_and_error(w, lib32, x_np, g_np, y_gpu):
+    from oracle import psfsim_oracle as O
+    cols, A_s = _oracle_sample(w, lib32)
+    per, reps = _oracle_step_time(w, A_s, cols, x_np, g_np)
+    base = {"value": 1.0 / per, "unit": "images/s", "cores": _cores(), "kind": "oracle",
+            "sample": f"FP64 NumPy oracle forward + adjoint on a {len(cols)}-column seeded sample of A "
+                      f"({len(cols)}/{w.K} columns, median of {reps} reps), extrapolated per column"}
+    rng = np.random.default_rng(29)
+    rows = np.sort(rng.choice(w.M, 64, replace=False))
+    xs, ys = O.scene_offsets(w.N, w.S)
+    A_r = O.A_rows(lib32.astype(np.float64), w.radii, xs, ys, rows)
+    x64 = x_np.astype(np.float64)
+    rel = O.bound_relative_error(y_gpu[rows], A_r @ x64, np.abs(A_r) @ np.abs(x64))
+    err = {"max_bound_rel_error": float(rel.max()), "median": float(np.median(rel)),
+           "rows_checked": int(len(rows)), "tolerance": 1e-5}
+    return base, err
+
+
+def _reference_arm(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return None
+    w, lib32, x_np, g_np = _workload()
+    cols, A_s = _oracle_sample(w, lib32)
+    _oracle_step_time(w, A_s, cols, x_np, g_np, max_steps=max(args.warmup, 1))
+    t0 = time.perf_counter()
+    per, reps = _oracle_step_time(w, A_s, cols, x_np, g_np, max_steps=args.steps)
+    wall = time.perf_counter() - t0
+    value = 1.0 / per
+    sample = (f"FP64 NumPy oracle forward + adjoint on a {len(cols)}-column seeded sample of A per step, "
+              f"extrapolated to all {w.K} columns ({wall:.1f} s wall for {reps} steps)")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "images/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{w.name}: n=N=128, s=S=0.25 lambda/D, 40 radii 0-12 lambda/D, "
+                                   "A 16384x16384; step = forward A x + adjoint A^T g",
+                       "M": w.M, "K": w.K, "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": "images/s", "cores": _cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "images/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="psfsim", choices=["psfsim", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local_rank = _dist()
+    if args.impl == "reference":
+        out = _reference_arm(args)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    out, plan, y, x_np, w, lib32 = _gpu_arm(args, rank, world, local_rank)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        _, _, _, g_np = _workload()
+        out["cpu_baseline"], out["error_vs_oracle"] = _cpu_baseline_and_error(
+            w, lib32, x_np, g_np, y.double().cpu().numpy() if y.dim() == 1 else y[0].double().cpu().numpy())
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

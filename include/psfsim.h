@@ -1,0 +1,139 @@
+/*
+ * psfsim: field-dependent coronagraphic image simulation on one GPU (sm_103a).
+ *
+ * The method (Milani & Douglas, "Faster imaging simulation through complex
+ * systems: a coronagraphic example", Sec. 2-3): a radial library of off-axis
+ * PSFs L[k] (offsets r_k along +x) is linearly interpolated in offset and
+ * rotated to the polar angle of every scene pixel; each result, flattened, is
+ * one column I_j of the matrix A = [I_1 ... I_K] (Eq. 4-5), and a simulated
+ * image is S = A Z for the flattened scene Z (Eq. 6).
+ *
+ * Conventions (all calls):
+ *   - Library d_lib: float32 [n_r][n][n], row p grows with +y, column q with +x,
+ *     optical axis at ((n-1)/2, (n-1)/2), PSF k's source at radii[k] along +x.
+ *   - Scene: N x N at S lambda/D per pixel, flattened row-major j = iy*N + ix,
+ *     pixel centre x_j = (ix - (N-1)/2) S, y_j = (iy - (N-1)/2) S (Eq. 2-3 with
+ *     the half-pixel shift).  Image: n x n, flattened i = p*n + q.  M = n*n,
+ *     K = N*N (or the number of field points).
+ *   - Radial weight: k = max{k : r_k <= r} clamped to [0, n_r-2],
+ *     w = (r - r_k)/(r_{k+1} - r_k) (>= 0); r > r_{n_r-1} gives a zero column.
+ *     PSFSIM_NEAREST rounds w to 0 or 1, ties to the lower radius.
+ *   - Rotation about the centre c = (n-1)/2, bilinear, taps outside the array
+ *     read 0: image pixel (p, q) samples column c + cos(q-c) + sin(p-c) and row
+ *     c - sin(q-c) + cos(p-c) of the interpolated PSF, cos = x/r, sin = y/r.
+ *   - Every device pointer is owned by the caller.  The library allocates no
+ *     device memory: A and its build-time tables live in the caller's
+ *     workspace, per-call temporaries in the caller's scratch.
+ *   - All calls are asynchronous on the given stream (a cudaStream_t passed as
+ *     void*; NULL is the legacy default stream) unless stated otherwise.
+ *   - Errors are returned, never raised: arguments are validated on the host
+ *     before anything is enqueued; a failed CUDA call maps to PSFSIM_ERR_CUDA.
+ */
+#ifndef PSFSIM_H
+#define PSFSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct psfsim_plan *psfsim_t; /* opaque host handle */
+
+enum psfsim_status {
+  PSFSIM_OK = 0,
+  PSFSIM_ERR_ARG = -1,         /* null pointer, bad size or enum */
+  PSFSIM_ERR_RADII = -2,       /* radii not finite and strictly increasing, or n_r < 2 */
+  PSFSIM_ERR_WORKSPACE = -3,   /* workspace / scratch too small or misaligned */
+  PSFSIM_ERR_CUDA = -4,        /* a CUDA runtime call failed */
+  PSFSIM_ERR_UNSUPPORTED = -5, /* valid request this build does not implement */
+  PSFSIM_ERR_TIMEOUT = -6      /* a bounded device-side wait gave up */
+};
+
+/* Storage of A.  FP32: column-major float32 (each PSF contiguous, as the
+ * paper saves one flattened PSF per iteration, Sec. 2).  SPLIT_BF16: row-major
+ * bf16 hi + lo with a power-of-two float32 scale per column, for the
+ * tensor-core path.  FUSED: A is never stored; tiles are regenerated from the
+ * library on every product (the paper's "standard interpolation method",
+ * Table 4, done on chip). */
+enum psfsim_storage { PSFSIM_FP32 = 0, PSFSIM_SPLIT_BF16 = 1, PSFSIM_FUSED = 3 };
+
+/* Radial interpolation (Sec. 2 compares linear and nearest). */
+enum psfsim_interp { PSFSIM_LINEAR = 0, PSFSIM_NEAREST = 1 };
+
+/* Layout of a built plan inside the caller's workspace (byte offsets). */
+typedef struct {
+  int32_t storage, interp, n, n_r;
+  int64_t M, K;
+  int64_t ld;           /* FP32: column stride in floats; SPLIT_BF16: row stride in elements */
+  int64_t a_offset;     /* FP32: A; SPLIT_BF16: hi */
+  int64_t lo_offset;    /* SPLIT_BF16: lo (else -1) */
+  int64_t scale_offset; /* SPLIT_BF16: float32 per-column scale (else -1) */
+  int64_t workspace_bytes;
+} psfsim_info_t;
+
+/* Human-readable name of a status code (static string). */
+const char *psfsim_status_string(int status);
+
+/* Bytes of workspace psfsim_build needs for an n x n library applied to an
+ * N x N scene (K = N*N columns) with the given storage.  Sec. 3: A has n^2
+ * rows and N^2 columns.  Returns PSFSIM_ERR_ARG for bad sizes. */
+int psfsim_workspace_bytes(int n, int64_t K, int storage, size_t *bytes);
+
+/* Build the interpolated PSF library A for a scene grid (Sec. 2, the loop over
+ * all N^2 scene pixels; Eq. 4-5).
+ *   d_lib       device float32 [n_r][n][n], 16-byte aligned; read during the
+ *               build, and kept (by pointer) for FUSED storage, so it must then
+ *               outlive the handle.
+ *   h_radii     host double [n_r], strictly increasing offsets in lambda/D.
+ *   s           PSF pixel scale (lambda/D per pixel).  A depends on s only
+ *               through the radii; it is validated (> 0).
+ *   N, S        scene size and pixel scale (lambda/D).
+ *   d_workspace device buffer of at least psfsim_workspace_bytes bytes,
+ *               256-byte aligned; holds A afterwards.
+ *   out         receives a host handle; release with psfsim_free.
+ * The build is enqueued on `stream`; A is valid once the stream reaches it. */
+int psfsim_build(const float *d_lib, const double *h_radii, int n_r, int n, double s,
+                 int N, double S, int storage, int interp, void *d_workspace,
+                 size_t workspace_bytes, void *stream, psfsim_t *out);
+
+/* Same as psfsim_build for K arbitrary field points h_xy (host double [K][2],
+ * (x, y) in lambda/D) instead of a scene grid; column j is the interpolated,
+ * rotated PSF of point j (Sec. 2 loop body).  Used for planets at sub-pixel
+ * offsets and for the exact invariants.  Copies h_xy synchronously. */
+int psfsim_build_points(const float *d_lib, const double *h_radii, int n_r, int n, double s,
+                        const double *h_xy, int64_t K, int storage, int interp,
+                        void *d_workspace, size_t workspace_bytes, void *stream, psfsim_t *out);
+
+/* Fill *info with the plan's layout. */
+int psfsim_info(psfsim_t h, psfsim_info_t *info);
+
+/* Scratch bytes psfsim_forward / psfsim_adjoint need for a batch of B. */
+int psfsim_forward_scratch_bytes(psfsim_t h, int B, size_t *bytes);
+int psfsim_adjoint_scratch_bytes(psfsim_t h, int B, size_t *bytes);
+
+/* Simulated images S = A Z (Eq. 6) for B scenes.
+ *   d_x  device float32 [B][K]; d_y device float32 [B][M] (written);
+ *   d_scratch at least psfsim_forward_scratch_bytes(h, B), 256-byte aligned.
+ * Deterministic: the same inputs give bitwise the same images. */
+int psfsim_forward(psfsim_t h, const float *d_x, int B, float *d_y, void *d_scratch,
+                   size_t scratch_bytes, void *stream);
+
+/* Transpose product g_x = A^T g for B image-space vectors (the adjoint of
+ * psfsim_forward; the paper's S = A Z read backwards, used for gradients).
+ *   d_g device float32 [B][M]; d_gx device float32 [B][K] (written). */
+int psfsim_adjoint(psfsim_t h, const float *d_g, int B, float *d_gx, void *d_scratch,
+                   size_t scratch_bytes, void *stream);
+
+/* Block until `stream` drains, then report a device-side status recorded by
+ * this plan's kernels (PSFSIM_ERR_TIMEOUT if a bounded wait gave up). */
+int psfsim_sync_status(psfsim_t h, void *stream);
+
+/* Release the host handle.  Device buffers stay the caller's. */
+void psfsim_free(psfsim_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSFSIM_H */

@@ -1,0 +1,76 @@
+"""ctypes declarations of libpsfsim's C ABI (include/psfsim.h, include/psfsim_fit.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Loading fails loudly when the library is missing; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpsfsim.so")
+
+OK, ERR_ARG, ERR_RADII, ERR_WORKSPACE, ERR_CUDA, ERR_UNSUPPORTED, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
+FP32, SPLIT_BF16, FUSED = 0, 1, 3
+LINEAR, NEAREST = 0, 1
+
+c_size_p = ctypes.POINTER(ctypes.c_size_t)
+vp = ctypes.c_void_p
+i32, i64, f64 = ctypes.c_int, ctypes.c_int64, ctypes.c_double
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("storage", ctypes.c_int32), ("interp", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("n_r", ctypes.c_int32), ("M", i64), ("K", i64), ("ld", i64), ("a_offset", i64),
+                ("lo_offset", i64), ("scale_offset", i64), ("workspace_bytes", i64)]
+
+
+# name -> (restype, argtypes); every symbol include/*.h declares.
+SIGNATURES = {
+    "psfsim_status_string": (ctypes.c_char_p, [i32]),
+    "psfsim_workspace_bytes": (i32, [i32, i64, i32, c_size_p]),
+    "psfsim_build": (i32, [vp, vp, i32, i32, f64, i32, f64, i32, i32, vp, ctypes.c_size_t, vp,
+                           ctypes.POINTER(vp)]),
+    "psfsim_build_points": (i32, [vp, vp, i32, i32, f64, vp, i64, i32, i32, vp, ctypes.c_size_t, vp,
+                                  ctypes.POINTER(vp)]),
+    "psfsim_info": (i32, [vp, ctypes.POINTER(Info)]),
+    "psfsim_forward_scratch_bytes": (i32, [vp, i32, c_size_p]),
+    "psfsim_adjoint_scratch_bytes": (i32, [vp, i32, c_size_p]),
+    "psfsim_forward": (i32, [vp, vp, i32, vp, vp, ctypes.c_size_t, vp]),
+    "psfsim_adjoint": (i32, [vp, vp, i32, vp, vp, ctypes.c_size_t, vp]),
+    "psfsim_sync_status": (i32, [vp, vp]),
+    "psfsim_free": (None, [vp]),
+}
+
+_lib = None
+
+
+class PsfsimError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {status_string(code)} ({code})")
+
+
+def load() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libpsfsim.so is not built ({LIB_PATH}); run __graft_entry__.build() "
+                               "or python -m paper_2106_09122_gb300.build_lib")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return load().psfsim_status_string(code).decode()
+
+
+def check(code: int, what: str) -> None:
+    if code != OK:
+        raise PsfsimError(code, what)

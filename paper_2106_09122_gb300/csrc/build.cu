@@ -1,0 +1,357 @@
+// Library build (Sec. 2): per-column geometry, bracket sort, and the kernels
+// that write every column of A = [I_1 ... I_K] (Eq. 4-5).
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
+#include "psfsim_internal.cuh"
+#include "ptx_util.cuh"
+
+namespace {
+
+constexpr double kFix = 1099511627776.0;  // 2^PSFSIM_FRAC_BITS
+static_assert(PSFSIM_FRAC_BITS == 40, "kFix");
+
+struct GeomParams {
+  int n_r, N, interp, pad;
+  int64_t K;
+  double S;
+  const double *pts;
+  double radii[PSFSIM_MAX_RADII];
+};
+
+// a1-a2: field offset (Eq. 2-3), polar angle as x/r, y/r, radial bracket + weight.
+__global__ void geom_kernel(const __grid_constant__ GeomParams P, ColGeom *geom) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= P.K) return;
+  double x, y;
+  if (P.pts) {
+    x = P.pts[2 * j];
+    y = P.pts[2 * j + 1];
+  } else {
+    const int iy = (int)(j / P.N), ix = (int)(j % P.N);
+    const double half = 0.5 * (double)(P.N - 1);
+    x = __dmul_rn((double)ix - half, P.S);
+    y = __dmul_rn((double)iy - half, P.S);
+  }
+  const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
+  double c = 1.0, s = 0.0;
+  if (r > 0.0) {
+    c = __ddiv_rn(x, r);
+    s = __ddiv_rn(y, r);
+  }
+  ColGeom g;
+  g.pad = 0;
+  g.C = __double2ll_rn(c * kFix);
+  g.Sn = __double2ll_rn(s * kFix);
+  if (!(r <= P.radii[P.n_r - 1])) {
+    g.k = -1;
+    g.w0 = 0.f;
+    g.w1 = 0.f;
+  } else {
+    int lo = 0, hi = P.n_r - 2;  // largest k in [0, n_r-2] with radii[k] <= r
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (P.radii[mid] <= r) lo = mid; else hi = mid - 1;
+    }
+    double w = __ddiv_rn(__dsub_rn(r, P.radii[lo]), __dsub_rn(P.radii[lo + 1], P.radii[lo]));
+    if (w < 0.0) w = 0.0;
+    if (P.interp == PSFSIM_NEAREST) w = (w > 0.5) ? 1.0 : 0.0;
+    g.k = lo;
+    g.w0 = (float)(1.0 - w);
+    g.w1 = (float)w;
+  }
+  geom[j] = g;
+}
+
+// Counting sort of the columns by radial bracket (bucket n_r-1 holds the zero
+// columns) so that a CTA can stage one bracket pair and build many columns.
+__global__ void __launch_bounds__(1024) bracket_sort_kernel(const ColGeom *geom, int64_t K, int n_r,
+                                                            int *order, int *bstart) {
+  __shared__ int cnt[PSFSIM_MAX_RADII + 1];
+  __shared__ int cur[PSFSIM_MAX_RADII + 1];
+  for (int b = threadIdx.x; b <= n_r; b += blockDim.x) cnt[b] = 0;
+  __syncthreads();
+  for (int64_t j = threadIdx.x; j < K; j += blockDim.x) {
+    const int k = geom[j].k;
+    atomicAdd(&cnt[k < 0 ? n_r - 1 : k], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int b = 0; b < n_r; ++b) {
+      bstart[b] = run;
+      cur[b] = run;
+      run += cnt[b];
+    }
+    bstart[n_r] = run;
+  }
+  __syncthreads();
+  for (int64_t j = threadIdx.x; j < K; j += blockDim.x) {
+    const int k = geom[j].k;
+    const int pos = atomicAdd(&cur[k < 0 ? n_r - 1 : k], 1);
+    order[pos] = (int)j;
+  }
+}
+
+struct BuildParams {
+  int n, n_r, Wp, pad;
+  int64_t K, ld;
+  const ColGeom *geom;
+  const int *order;
+  const int *bstart;
+  const float *lib;
+  float *A;
+  int *status;
+};
+
+// One rotated + lerped element (a3-a4).  a2/b2 hold 2a and 2b in fixed point
+// with PSFSIM_FRAC_BITS fraction bits; taps come from `tap(psf, row, col)`.
+template <typename TapFn>
+__device__ __forceinline__ float rotated_value(long long a2, long long b2, int n, float w0, float w1,
+                                               TapFn tap) {
+  constexpr int kShift = PSFSIM_FRAC_BITS + 1;
+  const int q0 = (int)(a2 >> kShift);
+  const int p0 = (int)(b2 >> kShift);
+  if (q0 < -1 || q0 > n - 1 || p0 < -1 || p0 > n - 1) return 0.f;
+  const unsigned fa = (unsigned)((unsigned long long)a2 >> (kShift - 32));
+  const unsigned fb = (unsigned)((unsigned long long)b2 >> (kShift - 32));
+  constexpr float kInv32 = 2.3283064365386963e-10f;  // 2^-32
+  const float wa1 = __uint2float_rn(fa) * kInv32;
+  const float wa0 = fa ? __uint2float_rn(0u - fa) * kInv32 : 1.f;
+  const float wb1 = __uint2float_rn(fb) * kInv32;
+  const float wb0 = fb ? __uint2float_rn(0u - fb) * kInv32 : 1.f;
+  float v0 = wb0 * (wa0 * tap(0, p0, q0) + wa1 * tap(0, p0, q0 + 1)) +
+             wb1 * (wa0 * tap(0, p0 + 1, q0) + wa1 * tap(0, p0 + 1, q0 + 1));
+  float v1 = 0.f;
+  if (w1 != 0.f)
+    v1 = wb0 * (wa0 * tap(1, p0, q0) + wa1 * tap(1, p0, q0 + 1)) +
+         wb1 * (wa0 * tap(1, p0 + 1, q0) + wa1 * tap(1, p0 + 1, q0 + 1));
+  return w0 * v0 + w1 * v1;
+}
+
+// Writes column j of A (FP32, column-major) with one warp.
+template <bool kSmem, bool kVec4>
+__device__ __forceinline__ void build_column(const BuildParams &P, int j, const float *s0,
+                                             const float *s1, int lane) {
+  const ColGeom g = P.geom[j];
+  float *col = P.A + (int64_t)j * P.ld;
+  const int n = P.n;
+  const int64_t M = (int64_t)n * n;
+  if (g.k < 0) {
+    for (int64_t i = lane; i < P.ld; i += 32) col[i] = 0.f;
+    return;
+  }
+  const float *L0 = P.lib + (int64_t)g.k * M;
+  const float *L1 = L0 + M;
+  const int Wp = P.Wp;
+  auto tap = [&](int which, int r, int c) -> float {
+    if (kSmem) {
+      const float *s = which ? s1 : s0;
+      return s[(r + 1) * Wp + (c + 4)];
+    } else {
+      if (r < 0 || r >= n || c < 0 || c >= n) return 0.f;
+      return __ldg((which ? L1 : L0) + r * n + c);
+    }
+  };
+  const long long h = n - 1;
+  const long long base = h << PSFSIM_FRAC_BITS;
+  if (kVec4) {
+    const int n4 = n >> 2;
+    int q4 = lane, p = 0;
+    while (q4 >= n4) { q4 -= n4; ++p; }
+    const int total = (int)(M >> 2);
+    for (int f = lane; f < total; f += 32) {
+      const int q = q4 << 2;
+      long long a2 = base + g.C * (2 * q - h) + g.Sn * (2 * p - h);
+      long long b2 = base - g.Sn * (2 * q - h) + g.C * (2 * p - h);
+      float4 v;
+      v.x = rotated_value(a2, b2, n, g.w0, g.w1, tap);
+      a2 += 2 * g.C; b2 -= 2 * g.Sn;
+      v.y = rotated_value(a2, b2, n, g.w0, g.w1, tap);
+      a2 += 2 * g.C; b2 -= 2 * g.Sn;
+      v.z = rotated_value(a2, b2, n, g.w0, g.w1, tap);
+      a2 += 2 * g.C; b2 -= 2 * g.Sn;
+      v.w = rotated_value(a2, b2, n, g.w0, g.w1, tap);
+      __stcs(reinterpret_cast<float4 *>(col + (int64_t)p * n + q), v);
+      q4 += 32;
+      while (q4 >= n4) { q4 -= n4; ++p; }
+    }
+  } else {
+    for (int64_t i = lane; i < M; i += 32) {
+      const int p = (int)(i / n), q = (int)(i % n);
+      const long long a2 = base + g.C * (2 * q - h) + g.Sn * (2 * p - h);
+      const long long b2 = base - g.Sn * (2 * q - h) + g.C * (2 * p - h);
+      col[i] = rotated_value(a2, b2, n, g.w0, g.w1, tap);
+    }
+  }
+  for (int64_t i = M + lane; i < P.ld; i += 32) col[i] = 0.f;
+}
+
+// Each CTA owns a contiguous range of the bracket-sorted column list; when the
+// bracket changes it stages L[k], L[k+1] (zero-padded by one pixel) in shared
+// memory with one TMA tensor load, then its warps build the columns.
+template <bool kSmem, bool kVec4>
+__global__ void __launch_bounds__(512) build_fp32_kernel(const __grid_constant__ CUtensorMap map,
+                                                         const BuildParams P) {
+  extern __shared__ __align__(128) float smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int64_t begin = P.K * blockIdx.x / gridDim.x;
+  const int64_t end = P.K * (blockIdx.x + 1) / gridDim.x;
+  float *s0 = smem;
+  float *s1 = smem + (P.n + 2) * P.Wp;
+  const uint32_t tx_bytes = 2u * (uint32_t)((P.n + 2) * P.Wp) * 4u;
+  if (kSmem && threadIdx.x == 0) {
+    ptx::mbar_init(&mbar, 1);
+    ptx::fence_mbar_init();
+  }
+  __syncthreads();
+  int cur_k = -2;
+  uint32_t phase = 0;
+  bool failed = false;
+  for (int64_t pos = begin; pos < end;) {
+    const int j0 = P.order[pos];
+    const int k = P.geom[j0].k;
+    const int bucket = k < 0 ? P.n_r - 1 : k;
+    const int64_t gend = min(end, (int64_t)P.bstart[bucket + 1]);
+    if (kSmem && k >= 0 && k != cur_k) {
+      __syncthreads();  // every warp is done with the previous pair
+      if (threadIdx.x == 0) {
+        ptx::mbar_arrive_expect_tx(&mbar, tx_bytes);
+        ptx::tma_load_3d(s0, &map, -4, -1, k, &mbar);
+      }
+      if (!ptx::mbar_wait_bounded(&mbar, phase)) failed = true;
+      phase ^= 1u;
+      cur_k = k;
+      if (__syncthreads_or(failed)) {
+        if (threadIdx.x == 0) atomicExch(P.status, PSFSIM_ERR_TIMEOUT);
+        return;
+      }
+    }
+    for (int64_t c = pos + warp; c < gend; c += nwarps)
+      build_column<kSmem, kVec4>(P, P.order[c], s0, s1, lane);
+    pos = gend;
+  }
+}
+
+}  // namespace
+
+WsLayout psfsim_layout(int n, int64_t K, int storage, int n_r) {
+  WsLayout L{};
+  const int64_t M = (int64_t)n * n;
+  int64_t off = 0;
+  auto take = [&](int64_t bytes) {
+    const int64_t at = off;
+    off = psfsim_round_up(off + bytes, 256);
+    return at;
+  };
+  L.lo_off = L.scale_off = -1;
+  if (storage == PSFSIM_FP32) {
+    L.ld = psfsim_round_up(M, 32);
+    L.a_off = take(L.ld * K * 4);
+  } else if (storage == PSFSIM_SPLIT_BF16) {
+    L.ld = psfsim_round_up(K, 64);
+    const int64_t rows = psfsim_round_up(M, 128);
+    L.a_off = take(rows * L.ld * 2);
+    L.lo_off = take(rows * L.ld * 2);
+    L.scale_off = take(L.ld * 4);
+  } else {  // FUSED: nothing but the tables
+    L.ld = 0;
+    L.a_off = -1;
+  }
+  L.geom_off = take(K * (int64_t)sizeof(ColGeom));
+  L.order_off = take(K * 4);
+  L.bstart_off = take((int64_t)(PSFSIM_MAX_RADII + 1) * 4);
+  L.pts_off = take(K * 16);
+  L.status_off = take(16);
+  L.total = off;
+  (void)n_r;
+  return L;
+}
+
+static bool encode_library_map(psfsim_plan *h, int Wp) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void *fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const int n = h->n;
+  cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)h->n_r};
+  cuuint64_t strides[2] = {(cuuint64_t)n * 4, (cuuint64_t)n * n * 4};
+  cuuint32_t box[3] = {(cuuint32_t)Wp, (cuuint32_t)(n + 2), 2};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode(&h->lib_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)h->d_lib, dims, strides, box,
+                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+cudaError_t psfsim_launch_build(psfsim_plan *h, cudaStream_t st) {
+  GeomParams G;
+  std::memset(&G, 0, sizeof(G));
+  G.n_r = h->n_r;
+  G.N = h->N;
+  G.interp = h->interp;
+  G.K = h->K;
+  G.S = h->S;
+  G.pts = h->N ? nullptr : reinterpret_cast<const double *>(h->ws + h->pts_off);
+  for (int i = 0; i < h->n_r; ++i) G.radii[i] = h->radii[i];
+  ColGeom *geom = reinterpret_cast<ColGeom *>(h->ws + h->geom_off);
+  int *order = reinterpret_cast<int *>(h->ws + h->order_off);
+  int *bstart = reinterpret_cast<int *>(h->ws + h->bstart_off);
+  int *status = reinterpret_cast<int *>(h->ws + h->status_off);
+  cudaError_t e = cudaMemsetAsync(status, 0, 16, st);
+  if (e != cudaSuccess) return e;
+  geom_kernel<<<(unsigned)((h->K + 255) / 256), 256, 0, st>>>(G, geom);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  bracket_sort_kernel<<<1, 1024, 0, st>>>(geom, h->K, h->n_r, order, bstart);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (h->storage == PSFSIM_FUSED) return cudaSuccess;
+  if (h->storage != PSFSIM_FP32) return cudaErrorNotSupported;
+
+  const int n = h->n;
+  const int Wp = (int)psfsim_round_up(n, 4) + 8;
+  const size_t smem = 2ull * (size_t)(n + 2) * Wp * 4;
+  const bool vec4 = (n % 4) == 0;
+  const bool use_smem = vec4 && smem <= 200 * 1024 && Wp <= 256 && encode_library_map(h, Wp);
+  h->lib_map_ok = use_smem;
+  BuildParams P;
+  P.n = n;
+  P.n_r = h->n_r;
+  P.Wp = Wp;
+  P.pad = 0;
+  P.K = h->K;
+  P.ld = h->ld;
+  P.geom = geom;
+  P.order = order;
+  P.bstart = bstart;
+  P.lib = h->d_lib;
+  P.A = reinterpret_cast<float *>(h->ws + h->a_off);
+  P.status = status;
+  CUtensorMap dummy;
+  std::memset(&dummy, 0, sizeof(dummy));
+  int threads = 512, per_sm = 1;
+  if (use_smem) {
+    threads = smem > 100 * 1024 ? 512 : 256;
+    auto kern = build_fp32_kernel<true, true>;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem)) != cudaSuccess)
+      return e;
+    per_sm = per_sm < 1 ? 1 : per_sm;
+    kern<<<h->num_sms * per_sm, threads, smem, st>>>(h->lib_map, P);
+  } else {
+    threads = 256;
+    per_sm = 8;
+    if (vec4)
+      build_fp32_kernel<false, true><<<h->num_sms * per_sm, threads, 0, st>>>(dummy, P);
+    else
+      build_fp32_kernel<false, false><<<h->num_sms * per_sm, threads, 0, st>>>(dummy, P);
+  }
+  return cudaGetLastError();
+}

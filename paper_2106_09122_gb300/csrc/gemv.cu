@@ -1,0 +1,207 @@
+// Products with a stored FP32 A (column-major, each PSF contiguous):
+//   forward  S = A Z   (Eq. 6): row-parallel, split over columns, partials in
+//            caller scratch, then a fixed-order reduction (deterministic);
+//   adjoint  A^T g:            one warp per column, warp-shuffle reduction.
+// Both stream A once from HBM with 128-bit loads that bypass L1.
+#include "psfsim_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ float4 ld_stream4(const float *p) {
+  float4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+
+constexpr int kFwdThreads = 256;
+constexpr int kRowsPerCta = kFwdThreads * 4;
+
+// part[(ks*B + b)*ld + r] = sum over the ks-th column chunk of A[r, j] x[b, j].
+template <int BB>
+__global__ void __launch_bounds__(kFwdThreads) fwd_partial_kernel(const float *__restrict__ A, int64_t ld,
+                                                                  int64_t K, const float *__restrict__ x,
+                                                                  int B, int b0, float *__restrict__ part) {
+  const int64_t r = (int64_t)blockIdx.x * kRowsPerCta + 4 * threadIdx.x;
+  const int KS = gridDim.y, ks = blockIdx.y;
+  const int64_t j0 = K * ks / KS, j1 = K * (ks + 1) / KS;
+  if (r >= ld) return;
+  float acc[BB][4];
+#pragma unroll
+  for (int b = 0; b < BB; ++b) acc[b][0] = acc[b][1] = acc[b][2] = acc[b][3] = 0.f;
+  const float *a = A + j0 * ld + r;
+  const float *xb = x + (int64_t)b0 * K;
+  int64_t j = j0;
+  for (; j + 4 <= j1; j += 4, a += 4 * ld) {
+    float4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = ld_stream4(a + u * ld);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+#pragma unroll
+      for (int b = 0; b < BB; ++b) {
+        const float xv = __ldg(xb + (int64_t)b * K + j + u);
+        acc[b][0] = fmaf(v[u].x, xv, acc[b][0]);
+        acc[b][1] = fmaf(v[u].y, xv, acc[b][1]);
+        acc[b][2] = fmaf(v[u].z, xv, acc[b][2]);
+        acc[b][3] = fmaf(v[u].w, xv, acc[b][3]);
+      }
+    }
+  }
+  for (; j < j1; ++j, a += ld) {
+    const float4 v = ld_stream4(a);
+#pragma unroll
+    for (int b = 0; b < BB; ++b) {
+      const float xv = __ldg(xb + (int64_t)b * K + j);
+      acc[b][0] = fmaf(v.x, xv, acc[b][0]);
+      acc[b][1] = fmaf(v.y, xv, acc[b][1]);
+      acc[b][2] = fmaf(v.z, xv, acc[b][2]);
+      acc[b][3] = fmaf(v.w, xv, acc[b][3]);
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < BB; ++b)
+    *reinterpret_cast<float4 *>(part + ((int64_t)ks * B + b0 + b) * ld + r) =
+        make_float4(acc[b][0], acc[b][1], acc[b][2], acc[b][3]);
+}
+
+// y[b, i] = sum_ks part[ks, b, i] in a fixed order.
+__global__ void fwd_reduce_kernel(const float *__restrict__ part, int KS, int B, int64_t ld, int64_t M,
+                                  float *__restrict__ y) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)B * M) return;
+  const int b = (int)(t / M);
+  const int64_t i = t % M;
+  float s = 0.f;
+  for (int ks = 0; ks < KS; ++ks) s += part[((int64_t)ks * B + b) * ld + i];
+  y[(int64_t)b * M + i] = s;
+}
+
+int forward_splits(const psfsim_plan *h) {
+  const int64_t row_blocks = (h->ld + kRowsPerCta - 1) / kRowsPerCta;
+  int64_t ks = (int64_t)h->num_sms * 8 / row_blocks;
+  ks = ks < 1 ? 1 : ks;
+  const int64_t max_ks = h->K / 8 > 0 ? h->K / 8 : 1;
+  return (int)(ks < max_ks ? ks : max_ks);
+}
+
+constexpr int kAdjThreads = 256;
+
+// gx[b, j] = sum_i A[i, j] g[b, i]; one warp per column.
+template <int BB, bool kVec>
+__global__ void __launch_bounds__(kAdjThreads) adj_kernel(const float *__restrict__ A, int64_t ld, int64_t M,
+                                                          int64_t K, const float *__restrict__ g, int b0,
+                                                          float *__restrict__ gx) {
+  const int64_t j = (int64_t)blockIdx.x * (kAdjThreads / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (j >= K) return;
+  const float *col = A + j * ld;
+  const float *gb = g + (int64_t)b0 * M;
+  float acc[BB];
+#pragma unroll
+  for (int b = 0; b < BB; ++b) acc[b] = 0.f;
+  if (kVec) {
+    const int64_t M4 = M >> 2;
+    int64_t i4 = lane;
+    for (; i4 + 96 < M4; i4 += 128) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = ld_stream4(col + 4 * (i4 + 32 * u));
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+#pragma unroll
+        for (int b = 0; b < BB; ++b) {
+          const float4 gv = __ldg(reinterpret_cast<const float4 *>(gb + (int64_t)b * M) + i4 + 32 * u);
+          acc[b] = fmaf(v[u].x, gv.x, acc[b]);
+          acc[b] = fmaf(v[u].y, gv.y, acc[b]);
+          acc[b] = fmaf(v[u].z, gv.z, acc[b]);
+          acc[b] = fmaf(v[u].w, gv.w, acc[b]);
+        }
+      }
+    }
+    for (; i4 < M4; i4 += 32) {
+      const float4 v = ld_stream4(col + 4 * i4);
+#pragma unroll
+      for (int b = 0; b < BB; ++b) {
+        const float4 gv = __ldg(reinterpret_cast<const float4 *>(gb + (int64_t)b * M) + i4);
+        acc[b] = fmaf(v.x, gv.x, acc[b]);
+        acc[b] = fmaf(v.y, gv.y, acc[b]);
+        acc[b] = fmaf(v.z, gv.z, acc[b]);
+        acc[b] = fmaf(v.w, gv.w, acc[b]);
+      }
+    }
+  } else {
+    for (int64_t i = lane; i < M; i += 32) {
+      const float v = __ldg(col + i);
+#pragma unroll
+      for (int b = 0; b < BB; ++b) acc[b] = fmaf(v, __ldg(gb + (int64_t)b * M + i), acc[b]);
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < BB; ++b) {
+    float s = acc[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) gx[(int64_t)(b0 + b) * K + j] = s;
+  }
+}
+
+template <int BB>
+cudaError_t fwd_group(const psfsim_plan *h, const float *x, int B, int b0, float *part, int KS,
+                      cudaStream_t st) {
+  const float *A = reinterpret_cast<const float *>(h->ws + h->a_off);
+  dim3 grid((unsigned)((h->ld + kRowsPerCta - 1) / kRowsPerCta), (unsigned)KS);
+  fwd_partial_kernel<BB><<<grid, kFwdThreads, 0, st>>>(A, h->ld, h->K, x, B, b0, part);
+  return cudaGetLastError();
+}
+
+template <int BB>
+cudaError_t adj_group(const psfsim_plan *h, const float *g, int b0, float *gx, bool vec, cudaStream_t st) {
+  const float *A = reinterpret_cast<const float *>(h->ws + h->a_off);
+  const unsigned grid = (unsigned)((h->K + kAdjThreads / 32 - 1) / (kAdjThreads / 32));
+  if (vec)
+    adj_kernel<BB, true><<<grid, kAdjThreads, 0, st>>>(A, h->ld, h->M, h->K, g, b0, gx);
+  else
+    adj_kernel<BB, false><<<grid, kAdjThreads, 0, st>>>(A, h->ld, h->M, h->K, g, b0, gx);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t psfsim_forward_fp32_scratch(const psfsim_plan *h, int B) {
+  return (size_t)forward_splits(h) * (size_t)B * (size_t)h->ld * 4;
+}
+
+cudaError_t psfsim_launch_forward_fp32(const psfsim_plan *h, const float *x, int B, float *y, void *scratch,
+                                       cudaStream_t st) {
+  const int KS = forward_splits(h);
+  float *part = reinterpret_cast<float *>(scratch);
+  cudaError_t e = cudaSuccess;
+  int b0 = 0;
+  while (b0 < B && e == cudaSuccess) {
+    const int left = B - b0;
+    if (left >= 8) { e = fwd_group<8>(h, x, B, b0, part, KS, st); b0 += 8; }
+    else if (left >= 4) { e = fwd_group<4>(h, x, B, b0, part, KS, st); b0 += 4; }
+    else if (left >= 2) { e = fwd_group<2>(h, x, B, b0, part, KS, st); b0 += 2; }
+    else { e = fwd_group<1>(h, x, B, b0, part, KS, st); b0 += 1; }
+  }
+  if (e != cudaSuccess) return e;
+  const int64_t total = (int64_t)B * h->M;
+  fwd_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(part, KS, B, h->ld, h->M, y);
+  return cudaGetLastError();
+}
+
+cudaError_t psfsim_launch_adjoint_fp32(const psfsim_plan *h, const float *g, int B, float *gx, cudaStream_t st) {
+  const bool vec = (h->M % 4 == 0) && ((reinterpret_cast<uintptr_t>(g) & 15) == 0);
+  cudaError_t e = cudaSuccess;
+  int b0 = 0;
+  while (b0 < B && e == cudaSuccess) {
+    const int left = B - b0;
+    if (left >= 8) { e = adj_group<8>(h, g, b0, gx, vec, st); b0 += 8; }
+    else if (left >= 4) { e = adj_group<4>(h, g, b0, gx, vec, st); b0 += 4; }
+    else if (left >= 2) { e = adj_group<2>(h, g, b0, gx, vec, st); b0 += 2; }
+    else { e = adj_group<1>(h, g, b0, gx, vec, st); b0 += 1; }
+  }
+  return e;
+}

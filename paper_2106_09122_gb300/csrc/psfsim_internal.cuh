@@ -1,0 +1,61 @@
+// Internal declarations shared by the psfsim CUDA translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/psfsim.h"
+
+#define PSFSIM_MAX_RADII 256
+#define PSFSIM_FRAC_BITS 40  // fixed-point fraction bits of the rotation coordinates
+
+// Per-column geometry, computed once per build on the device (FP64, Sec. 2):
+// radial bracket k (-1: beyond the last radius, zero column), the two lerp
+// weights, and cos/sin of the polar angle as fixed-point integers
+// round(v * 2^PSFSIM_FRAC_BITS).  Exact integer arithmetic on these makes
+// theta = 0 the identity and quarter turns exact permutations.
+struct ColGeom {
+  int k;
+  int pad;
+  float w0, w1;  // weights of L[k] and L[k+1]
+  long long C, Sn;
+};
+static_assert(sizeof(ColGeom) == 32, "ColGeom layout");
+
+struct psfsim_plan {
+  int storage, interp, n, n_r;
+  int64_t M, K, ld;
+  int N;          // scene side for grid builds, 0 for point builds
+  double S, s;
+  const float *d_lib;
+  double radii[PSFSIM_MAX_RADII];
+  char *ws;
+  size_t ws_bytes;
+  int64_t a_off, lo_off, scale_off, geom_off, order_off, bstart_off, pts_off, status_off;
+  int device, num_sms;
+  bool lib_map_ok;
+  CUtensorMap lib_map;  // 3D tensor map over the library for TMA staging
+};
+
+// Workspace layout for a given shape; returns total bytes.
+struct WsLayout {
+  int64_t ld, a_off, lo_off, scale_off, geom_off, order_off, bstart_off, pts_off, status_off, total;
+};
+WsLayout psfsim_layout(int n, int64_t K, int storage, int n_r);
+
+// Kernel launchers (return cudaError_t of the launch).
+cudaError_t psfsim_launch_build(psfsim_plan *h, cudaStream_t st);
+cudaError_t psfsim_launch_forward_fp32(const psfsim_plan *h, const float *x, int B, float *y,
+                                       void *scratch, cudaStream_t st);
+size_t psfsim_forward_fp32_scratch(const psfsim_plan *h, int B);
+cudaError_t psfsim_launch_adjoint_fp32(const psfsim_plan *h, const float *g, int B, float *gx,
+                                       cudaStream_t st);
+
+static inline int64_t psfsim_round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+#define PSFSIM_CUDA_TRY(expr)                 \
+  do {                                        \
+    cudaError_t _e = (expr);                  \
+    if (_e != cudaSuccess) return PSFSIM_ERR_CUDA; \
+  } while (0)
