@@ -120,6 +120,30 @@ int psfsim_adjoint_scratch_bytes(psfsim_t h, int B, size_t *bytes);
 int psfsim_forward(psfsim_t h, const float *d_x, int B, float *d_y, void *d_scratch,
                    size_t scratch_bytes, void *stream);
 
+/* Capacity of the fixed device array psfsim_forward_static works in. */
+#define PSFSIM_STATIC_SCRATCH_BYTES ((size_t)16 * 1024 * 1024)
+
+/* psfsim_forward without caller scratch, for callers that cannot allocate
+ * device memory when they simulate an image and have no spare buffer to pass:
+ * a plug-in running inside a host application that owns the GPU's allocator,
+ * or a fixed-memory loop that may not grow its footprint after start-up.  The
+ * paper has no counterpart; this is a deployment convenience.
+ *   Same arguments and result as psfsim_forward (FP32 storage only), but the
+ *   partial sums live in a PSFSIM_STATIC_SCRATCH_BYTES array compiled into
+ *   the library; every GPU that loads the library holds it until exit.
+ *   Nothing is allocated: no cudaMalloc, no cudaFree, no allocating library call.
+ *   Returns PSFSIM_ERR_WORKSPACE when this plan's partial sums for B scenes
+ *   (psfsim_forward_scratch_bytes(h, B)) exceed PSFSIM_STATIC_SCRATCH_BYTES,
+ *   PSFSIM_ERR_ARG when the current device is not the plan's device.
+ *   The first call on a device looks up the array's device address (a
+ *   cudaGetSymbolAddress, done once per device with it current); make that
+ *   first call before any stream capture.
+ *   All calls share the one array: calls whose kernels overlap on the GPU
+ *   (other streams, other threads, other plans) race and corrupt each
+ *   other's images.  Calls ordered on one stream are safe; leftover contents
+ *   from an earlier call are always overwritten before they are read. */
+int psfsim_forward_static(psfsim_t h, const float *d_x, int B, float *d_y, void *stream);
+
 /* Transpose product g_x = A^T g for B image-space vectors (the adjoint of
  * psfsim_forward; the paper's S = A Z read backwards, used for gradients).
  *   d_g device float32 [B][M]; d_gx device float32 [B][K] (written). */

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "libpsfsim.so")
 OK, ERR_ARG, ERR_RADII, ERR_WORKSPACE, ERR_CUDA, ERR_UNSUPPORTED, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
 FP32, SPLIT_BF16, FUSED = 0, 1, 3
 LINEAR, NEAREST = 0, 1
+STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
 
 c_size_p = ctypes.POINTER(ctypes.c_size_t)
 vp = ctypes.c_void_p
@@ -39,6 +40,7 @@ SIGNATURES = {
     "psfsim_adjoint_scratch_bytes": (i32, [vp, i32, c_size_p]),
     "psfsim_forward": (i32, [vp, vp, i32, vp, vp, ctypes.c_size_t, vp]),
     "psfsim_adjoint": (i32, [vp, vp, i32, vp, vp, ctypes.c_size_t, vp]),
+    "psfsim_forward_static": (i32, [vp, vp, i32, vp, vp]),
     "psfsim_sync_status": (i32, [vp, vp]),
     "psfsim_free": (None, [vp]),
 }
