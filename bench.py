@@ -3,9 +3,10 @@
 Workload (default): the 128 x 128 adjoint/fit configuration -- 40 synthetic
 Lyot PSFs of 128^2 at 0.25 lambda/D, a 128^2 scene, A = 16384 x 16384 FP32
 (1.07 GB, larger than L2, so no flush is needed between steps).  One step is
-one gradient evaluation of the ring fit's inner loop: the forward image
-S = A Z (Eq. 6) and the adjoint A^T g of an image-space residual, i.e. two
-full passes over A.  value = images simulated per second (one per step).
+one gradient evaluation of the ring fit: ring scene Z(theta), the forward
+image S = A Z (Eq. 6), the float64 loss and residual, the adjoint A^T r and
+the chain rule into the 5 ring parameters -- two full passes over A.
+value = images simulated per second (one per step).
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -108,86 +109,92 @@ def _workload():
     return w, lib32, x, g
 
 
+def _events(n):
+    import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
 def _gpu_arm(args, rank, world, local_rank):
     import torch
     from paper_2106_09122_gb300 import Plan
+    from paper_2106_09122_gb300.fit import RingProblem
+    from synth import workloads
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     w, lib32, x_np, g_np = _workload()
     stream = torch.cuda.current_stream()
-    plan = Plan(torch.from_numpy(lib32).to(dev), w.radii, w.s, N=w.N, S=w.S)
-    x = torch.from_numpy(x_np).to(dev)
-    g = torch.from_numpy(g_np).to(dev)
-    y = torch.empty(w.M, dtype=torch.float32, device=dev)
-    gx = torch.empty(w.K, dtype=torch.float32, device=dev)
-    fscr = torch.empty(max(plan.forward_scratch_bytes(1), 1), dtype=torch.uint8, device=dev)
-    ascr = torch.empty(max(plan.adjoint_scratch_bytes(1), 1), dtype=torch.uint8, device=dev)
+    lib_d = torch.from_numpy(lib32).to(dev)
 
-    # build timing (one-off, context for the paper's Table 2)
+    # one-off library build (the paper's Table 2 step), timed on its own
     torch.cuda.synchronize()
-    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0, b1 = _events(2)
     b0.record(stream)
-    plan2 = Plan(plan.lib, w.radii, w.s, N=w.N, S=w.S)
+    plan = Plan(lib_d, w.radii, w.s, N=w.N, S=w.S)
     b1.record(stream)
     torch.cuda.synchronize()
     build_ms = b0.elapsed_time(b1)
-    del plan2
 
-    def step():
-        plan.forward(x, out=y, scratch=fscr)
-        plan.adjoint(g, out=gx, scratch=ascr)
+    # target image: noisy simulated truth (the fit workload's inputs)
+    truth = np.array(w.extra["truth"])
+    sigma = w.extra["sigma"]
+    tmp = RingProblem(plan, w.N, w.S, w.r_max, torch.zeros(w.M, device=dev), sigma)
+    d = plan.forward(tmp.scene(truth).clone()) + torch.from_numpy(
+        workloads.fit_target_noise(w, w.M).astype(np.float32)).to(dev)
+    prob = RingProblem(plan, w.N, w.S, w.r_max, d, sigma)
+    theta = workloads.fit_init(w)
 
     for _ in range(args.warmup):
-        step()
+        prob.enqueue_gradient(theta)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     nsteps = args.steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+    ev = [_events(4) for _ in range(nsteps)]
     clocks = ClockSampler(local_rank)
     clocks.start()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
+    t0, t1 = _events(2)
+    prob.launches = 0
     t0.record(stream)
     for i in range(nsteps):
+        # one gradient evaluation: ring -> forward -> loss -> adjoint -> chain
         ev[i][0].record(stream)
-        plan.forward(x, out=y, scratch=fscr)
+        prob.plan.forward(prob.scene(theta), out=prob.y, scratch=prob.fscr)
         ev[i][1].record(stream)
-        plan.adjoint(g, out=gx, scratch=ascr)
+        prob.residual_loss(prob.y, prob.target, True)
         ev[i][2].record(stream)
+        prob.plan.adjoint(prob.r, out=prob.gz, scratch=prob.ascr)
+        ev[i][3].record(stream)
+        prob.chain(theta, prob.gz)
     t1.record(stream)
     torch.cuda.synchronize()
+    launches = prob.launches + 3 * nsteps
     clk = clocks.stop()
     elapsed_ms = t0.elapsed_time(t1)
-    fwd_ms = float(np.mean([a.elapsed_time(b) for a, b, _ in ev]))
-    adj_ms = float(np.mean([b.elapsed_time(c) for _, b, c in ev]))
+    fwd_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+    adj_ms = float(np.mean([e[2].elapsed_time(e[3]) for e in ev]))
     if world > 1:
         t = torch.tensor([elapsed_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         elapsed_ms = float(t.item())
 
-    # e2e: host buffers through the same C-ABI calls, copies inside the timed region
-    hx = torch.from_numpy(x_np).pin_memory()
-    hg = torch.from_numpy(g_np).pin_memory()
-    hy = torch.empty(w.M, dtype=torch.float32).pin_memory()
-    hgx = torch.empty(w.K, dtype=torch.float32).pin_memory()
-    dx = torch.empty_like(x)
-    dg = torch.empty_like(g)
+    # e2e: a new observed image arrives from pinned host memory every step and
+    # the loss + gradient come back to the host, through the same C-ABI calls
+    hd = d.cpu().pin_memory()
+    hout = torch.empty(6, dtype=torch.float64).pin_memory()
+    dd = torch.empty_like(d)
+    prob_e = RingProblem(plan, w.N, w.S, w.r_max, dd, sigma)
 
     def e2e_step():
-        dx.copy_(hx, non_blocking=True)
-        dg.copy_(hg, non_blocking=True)
-        plan.forward(dx, out=y, scratch=fscr)
-        plan.adjoint(dg, out=gx, scratch=ascr)
-        hy.copy_(y, non_blocking=True)
-        hgx.copy_(gx, non_blocking=True)
+        dd.copy_(hd, non_blocking=True)
+        prob_e.enqueue_gradient(theta)
+        hout[:1].copy_(prob_e.loss_d, non_blocking=True)
+        hout[1:].copy_(prob_e.dtheta, non_blocking=True)
 
     for _ in range(args.warmup):
         e2e_step()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0, e1 = _events(2)
     e0.record(stream)
     for _ in range(nsteps):
         e2e_step()
@@ -200,11 +207,14 @@ def _gpu_arm(args, rank, world, local_rank):
         e2e_ms = float(t.item())
 
     # plain FP32 GEMV comparator (cuBLAS through torch) on the same stored A
+    x = torch.from_numpy(x_np).to(dev)
+    g = torch.from_numpy(g_np).to(dev)
     A = plan.A_fp32()
     for _ in range(3):
         torch.mv(A, x)
+        torch.mv(A.t(), g)
     torch.cuda.synchronize()
-    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0, c1 = _events(2)
     c0.record(stream)
     for _ in range(nsteps):
         torch.mv(A, x)
@@ -212,14 +222,24 @@ def _gpu_arm(args, rank, world, local_rank):
     c1.record(stream)
     torch.cuda.synchronize()
     cmp_ms = c0.elapsed_time(c1) / nsteps
-    y_ref_cublas = torch.mv(A, x)
-    agree = float(((plan.forward(x) - y_ref_cublas).abs().max() / y_ref_cublas.abs().max()).item())
+    y_gpu = plan.forward(x)
+    y_cublas = torch.mv(A, x)
+    agree = float(((y_gpu - y_cublas).abs().max() / y_cublas.abs().max()).item())
+
+    # the 200-step fit itself (host line search reads the float64 loss each trial)
+    torch.cuda.synchronize()
+    f0 = time.perf_counter()
+    theta_fit, hist = prob.fit(theta, steps=w.extra["steps"])
+    fit_s = time.perf_counter() - f0
 
     hbm, _, peak_kind = _peaks()
     a_bytes = w.M * w.K * 4
     fwd_bytes = a_bytes + w.K * 4 + w.M * 4
+    adj_bytes = a_bytes + w.M * 4 + w.K * 4
     ms_per_step = elapsed_ms / nsteps
     images = world * nsteps
+    dominant = "adjoint" if adj_ms > fwd_ms else "forward"
+    dom_ms, dom_bytes = (adj_ms, adj_bytes) if dominant == "adjoint" else (fwd_ms, fwd_bytes)
     out = {
         "metric": METRIC,
         "value": images / (elapsed_ms / 1e3),
@@ -234,26 +254,32 @@ def _gpu_arm(args, rank, world, local_rank):
         "dtype": "f32",
         "data": "synthetic (seeded Lyot-coronagraph PSFs, exozodi ring scene)",
         "config": {"workload": f"{w.name}: n=N=128, s=S=0.25 lambda/D, 40 radii 0-12 lambda/D, "
-                               "A 16384x16384 FP32; step = forward A x + adjoint A^T g",
+                               "A 16384x16384 FP32; step = one fit gradient: ring Z(theta), S = A Z, "
+                               "FP64 loss, A^T r, chain to 5 ring parameters",
                    "M": w.M, "K": w.K, "n_radii": len(w.radii), "storage": "fp32",
                    "l2": "inputs larger than L2 (A is 1.07 GB), no flush",
                    "parallelism": f"replicas x{world}"},
         "gmac_per_s": images * 2 * w.M * w.K / (elapsed_ms / 1e3) / 1e9,
         "kernels_ms": {"forward": fwd_ms, "adjoint": adj_ms, "build_once": build_ms},
-        "roofline": {"bound": "hbm", "achieved": fwd_bytes / (fwd_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-                     "frac": fwd_bytes / (fwd_ms / 1e3) / 1e9 / hbm, "traffic": None,
-                     "kernel": "psfsim forward (fwd_partial_kernel + fwd_reduce_kernel)",
+        "roofline": {"bound": "hbm", "achieved": dom_bytes / (dom_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": dom_bytes / (dom_ms / 1e3) / 1e9 / hbm, "traffic": None,
+                     "kernel": f"psfsim {dominant} (A streamed once per launch)",
                      "peak_source": f"{peak_kind} hbm_gbs"},
-        "adjoint_roofline_frac": (a_bytes + w.K * 4 + w.M * 4) / (adj_ms / 1e3) / 1e9 / hbm,
+        "roofline_frac": {"forward": fwd_bytes / (fwd_ms / 1e3) / 1e9 / hbm,
+                          "adjoint": adj_bytes / (adj_ms / 1e3) / 1e9 / hbm},
         "fp32_gemv_comparator": {"impl": "torch.mv (cuBLAS) forward + adjoint on the same A",
                                  "ms_per_step": cmp_ms, "images_per_s": 1e3 / cmp_ms,
+                                 "psfsim_forward_adjoint_ms": fwd_ms + adj_ms,
                                  "max_rel_diff_vs_psfsim": agree},
+        "fit": {"steps": int(len(hist) - 1), "seconds": fit_s, "loss_first": float(hist[0]),
+                "loss_last": float(hist[-1]), "theta": [float(v) for v in theta_fit],
+                "truth": [float(v) for v in truth]},
         "e2e": {"value": images / (e2e_ms / 1e3), "unit": "images/s",
-                "h2d_bytes_per_step": (w.K + w.M) * 4, "d2h_bytes_per_step": (w.M + w.K) * 4},
-        "gpu_launches": nsteps * 3,
+                "h2d_bytes_per_step": w.M * 4, "d2h_bytes_per_step": 6 * 8},
+        "gpu_launches": launches,
         "clocks": clk,
     }
-    return out, plan, y, x_np, w, lib32
+    return out, plan, y_gpu, x_np, w, lib32
 
 
 def _oracle_sample(w, lib32, n_cols=512, seed=17):
@@ -354,7 +380,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         _, _, _, g_np = _workload()
         out["cpu_baseline"], out["error_vs_oracle"] = _cpu_baseline_and_error(
-            w, lib32, x_np, g_np, y.double().cpu().numpy() if y.dim() == 1 else y[0].double().cpu().numpy())
+            w, lib32, x_np, g_np, y.double().cpu().numpy())
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -42,6 +42,11 @@ SIGNATURES = {
     "psfsim_adjoint": (i32, [vp, vp, i32, vp, vp, ctypes.c_size_t, vp]),
     "psfsim_forward_static": (i32, [vp, vp, i32, vp, vp]),
     "psfsim_sync_status": (i32, [vp, vp]),
+    "psfsim_ring_chain_scratch_bytes": (i32, [i32, c_size_p]),
+    "psfsim_loss_scratch_bytes": (i32, [i64, c_size_p]),
+    "psfsim_ring_scene": (i32, [i32, f64, f64, vp, vp, vp]),
+    "psfsim_ring_chain": (i32, [i32, f64, f64, vp, vp, vp, vp, ctypes.c_size_t, vp]),
+    "psfsim_residual_loss": (i32, [vp, vp, i64, f64, vp, vp, vp, ctypes.c_size_t, vp]),
     "psfsim_free": (None, [vp]),
 }
 

@@ -1,7 +1,8 @@
 // Products with a stored FP32 A (column-major, each PSF contiguous):
 //   forward  S = A Z   (Eq. 6): row-parallel, split over columns, partials in
 //            caller scratch, then a fixed-order reduction (deterministic);
-//   adjoint  A^T g:            one warp per column, warp-shuffle reduction.
+//   adjoint  A^T g:            contiguous column ranges per CTA, rows split
+//            across the CTA, fixed-order reduction.
 // Both stream A once from HBM with 128-bit loads that bypass L1.
 #include "psfsim_internal.cuh"
 
@@ -66,16 +67,42 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_partial_kernel(const float *_
         make_float4(acc[b][0], acc[b][1], acc[b][2], acc[b][3]);
 }
 
-// y[b, i] = sum_ks part[ks, b, i] in a fixed order.
-__global__ void fwd_reduce_kernel(const float *__restrict__ part, int KS, int B, int64_t ld, int64_t M,
-                                  float *__restrict__ y) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= (int64_t)B * M) return;
-  const int b = (int)(t / M);
-  const int64_t i = t % M;
-  float s = 0.f;
-  for (int ks = 0; ks < KS; ++ks) s += part[((int64_t)ks * B + b) * ld + i];
-  y[(int64_t)b * M + i] = s;
+// y[b, i] = sum_ks part[ks, b, i] in a fixed order.  A CTA covers 128 rows;
+// its 8 warps split the KS partials (ks = warp, warp + 8, ...) and combine
+// through shared memory, so every output needs only ~KS/8 loads per thread.
+constexpr int kRedRows = 128;
+__global__ void __launch_bounds__(256) fwd_reduce_kernel(const float *__restrict__ part, int KS, int B,
+                                                         int64_t ld, int64_t M, float *__restrict__ y) {
+  __shared__ float4 red[8][32];
+  const int c4 = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  const int64_t r = ((int64_t)blockIdx.x * 32 + c4) * 4;
+  const int b = blockIdx.y;
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (r < ld) {
+    const float *p = part + (int64_t)b * ld + r;
+    const int64_t step = (int64_t)B * ld;
+    int ks = grp;
+#pragma unroll 4
+    for (; ks < KS; ks += 8) {
+      const float4 v = *reinterpret_cast<const float4 *>(p + ks * step);
+      s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+    }
+  }
+  red[grp][c4] = s;
+  __syncthreads();
+  if (grp == 0 && r < M) {
+    float4 t = red[0][c4];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) {
+      const float4 v = red[k][c4];
+      t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w;
+    }
+    float *out = y + (int64_t)b * M + r;
+    out[0] = t.x;
+    if (r + 1 < M) out[1] = t.y;
+    if (r + 2 < M) out[2] = t.z;
+    if (r + 3 < M) out[3] = t.w;
+  }
 }
 
 int forward_splits(const psfsim_plan *h) {
@@ -88,62 +115,76 @@ int forward_splits(const psfsim_plan *h) {
 
 constexpr int kAdjThreads = 256;
 
-// gx[b, j] = sum_i A[i, j] g[b, i]; one warp per column.
+// gx[b, j] = sum_i A[i, j] g[b, i].  CTA c owns the contiguous column range
+// [K c / G, K (c+1) / G); for each column its 256 threads split the rows
+// (float4 strided), reduce in registers, then across warps through a
+// double-buffered shared array.  Fixed assignment and order: deterministic.
 template <int BB, bool kVec>
 __global__ void __launch_bounds__(kAdjThreads) adj_kernel(const float *__restrict__ A, int64_t ld, int64_t M,
                                                           int64_t K, const float *__restrict__ g, int b0,
                                                           float *__restrict__ gx) {
-  const int64_t j = (int64_t)blockIdx.x * (kAdjThreads / 32) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (j >= K) return;
-  const float *col = A + j * ld;
+  __shared__ float red[2][kAdjThreads / 32][BB];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t j0 = K * blockIdx.x / gridDim.x, j1 = K * (blockIdx.x + 1) / gridDim.x;
   const float *gb = g + (int64_t)b0 * M;
-  float acc[BB];
+  int parity = 0;
+  for (int64_t j = j0; j < j1; ++j, parity ^= 1) {
+    const float *col = A + j * ld;
+    float acc[BB];
 #pragma unroll
-  for (int b = 0; b < BB; ++b) acc[b] = 0.f;
-  if (kVec) {
-    const int64_t M4 = M >> 2;
-    int64_t i4 = lane;
-    for (; i4 + 96 < M4; i4 += 128) {
-      float4 v[4];
+    for (int b = 0; b < BB; ++b) acc[b] = 0.f;
+    if (kVec) {
+      const int64_t M4 = M >> 2;
+      int64_t i4 = threadIdx.x;
+      constexpr int T = kAdjThreads;
+      for (; i4 + 3 * T < M4; i4 += 4 * T) {
+        float4 v[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] = ld_stream4(col + 4 * (i4 + 32 * u));
+        for (int u = 0; u < 4; ++u) v[u] = ld_stream4(col + 4 * (i4 + T * u));
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 4; ++u) {
 #pragma unroll
-        for (int b = 0; b < BB; ++b) {
-          const float4 gv = __ldg(reinterpret_cast<const float4 *>(gb + (int64_t)b * M) + i4 + 32 * u);
-          acc[b] = fmaf(v[u].x, gv.x, acc[b]);
-          acc[b] = fmaf(v[u].y, gv.y, acc[b]);
-          acc[b] = fmaf(v[u].z, gv.z, acc[b]);
-          acc[b] = fmaf(v[u].w, gv.w, acc[b]);
+          for (int b = 0; b < BB; ++b) {
+            const float4 gv = __ldg(reinterpret_cast<const float4 *>(gb + (int64_t)b * M) + i4 + T * u);
+            acc[b] = fmaf(v[u].x, gv.x, acc[b]);
+            acc[b] = fmaf(v[u].y, gv.y, acc[b]);
+            acc[b] = fmaf(v[u].z, gv.z, acc[b]);
+            acc[b] = fmaf(v[u].w, gv.w, acc[b]);
+          }
         }
       }
-    }
-    for (; i4 < M4; i4 += 32) {
-      const float4 v = ld_stream4(col + 4 * i4);
+      for (; i4 < M4; i4 += T) {
+        const float4 v = ld_stream4(col + 4 * i4);
 #pragma unroll
-      for (int b = 0; b < BB; ++b) {
-        const float4 gv = __ldg(reinterpret_cast<const float4 *>(gb + (int64_t)b * M) + i4);
-        acc[b] = fmaf(v.x, gv.x, acc[b]);
-        acc[b] = fmaf(v.y, gv.y, acc[b]);
-        acc[b] = fmaf(v.z, gv.z, acc[b]);
-        acc[b] = fmaf(v.w, gv.w, acc[b]);
+        for (int b = 0; b < BB; ++b) {
+          const float4 gv = __ldg(reinterpret_cast<const float4 *>(gb + (int64_t)b * M) + i4);
+          acc[b] = fmaf(v.x, gv.x, acc[b]);
+          acc[b] = fmaf(v.y, gv.y, acc[b]);
+          acc[b] = fmaf(v.z, gv.z, acc[b]);
+          acc[b] = fmaf(v.w, gv.w, acc[b]);
+        }
+      }
+    } else {
+      for (int64_t i = threadIdx.x; i < M; i += kAdjThreads) {
+        const float v = __ldg(col + i);
+#pragma unroll
+        for (int b = 0; b < BB; ++b) acc[b] = fmaf(v, __ldg(gb + (int64_t)b * M + i), acc[b]);
       }
     }
-  } else {
-    for (int64_t i = lane; i < M; i += 32) {
-      const float v = __ldg(col + i);
 #pragma unroll
-      for (int b = 0; b < BB; ++b) acc[b] = fmaf(v, __ldg(gb + (int64_t)b * M + i), acc[b]);
+    for (int b = 0; b < BB; ++b) {
+      float s = acc[b];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) red[parity][warp][b] = s;
     }
-  }
+    __syncthreads();
+    if (threadIdx.x < BB) {
+      float t = red[parity][0][threadIdx.x];
 #pragma unroll
-  for (int b = 0; b < BB; ++b) {
-    float s = acc[b];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) gx[(int64_t)(b0 + b) * K + j] = s;
+      for (int w = 1; w < kAdjThreads / 32; ++w) t += red[parity][w][threadIdx.x];
+      gx[(int64_t)(b0 + threadIdx.x) * K + j] = t;
+    }
   }
 }
 
@@ -159,11 +200,13 @@ cudaError_t fwd_group(const psfsim_plan *h, const float *x, int B, int b0, float
 template <int BB>
 cudaError_t adj_group(const psfsim_plan *h, const float *g, int b0, float *gx, bool vec, cudaStream_t st) {
   const float *A = reinterpret_cast<const float *>(h->ws + h->a_off);
-  const unsigned grid = (unsigned)((h->K + kAdjThreads / 32 - 1) / (kAdjThreads / 32));
-  if (vec)
-    adj_kernel<BB, true><<<grid, kAdjThreads, 0, st>>>(A, h->ld, h->M, h->K, g, b0, gx);
-  else
-    adj_kernel<BB, false><<<grid, kAdjThreads, 0, st>>>(A, h->ld, h->M, h->K, g, b0, gx);
+  auto kern = vec ? adj_kernel<BB, true> : adj_kernel<BB, false>;
+  int per_sm = 1;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kAdjThreads, 0);
+  if (e != cudaSuccess) return e;
+  int64_t grid = (int64_t)h->num_sms * (per_sm < 1 ? 1 : per_sm);
+  if (grid > h->K) grid = h->K;
+  kern<<<(unsigned)grid, kAdjThreads, 0, st>>>(A, h->ld, h->M, h->K, g, b0, gx);
   return cudaGetLastError();
 }
 
@@ -187,8 +230,8 @@ cudaError_t psfsim_launch_forward_fp32(const psfsim_plan *h, const float *x, int
     else { e = fwd_group<1>(h, x, B, b0, part, KS, st); b0 += 1; }
   }
   if (e != cudaSuccess) return e;
-  const int64_t total = (int64_t)B * h->M;
-  fwd_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(part, KS, B, h->ld, h->M, y);
+  dim3 grid((unsigned)((h->ld + kRedRows - 1) / kRedRows), (unsigned)B);
+  fwd_reduce_kernel<<<grid, 256, 0, st>>>(part, KS, B, h->ld, h->M, y);
   return cudaGetLastError();
 }
 
