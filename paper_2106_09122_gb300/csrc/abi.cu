@@ -34,7 +34,7 @@ int common_build(const float *d_lib, const double *h_radii, int n_r, int n, doub
   if (!storage_ok(storage) || (interp != PSFSIM_LINEAR && interp != PSFSIM_NEAREST)) return PSFSIM_ERR_ARG;
   if (!aligned(d_lib, 16)) return PSFSIM_ERR_ARG;
   if (int rc = check_radii(h_radii, n_r)) return rc;
-  if (storage != PSFSIM_FP32) return PSFSIM_ERR_UNSUPPORTED;
+  if (storage == PSFSIM_FUSED) return PSFSIM_ERR_UNSUPPORTED;
   const WsLayout L = psfsim_layout(n, K, storage, n_r);
   if (!aligned(d_ws, 256) || ws_bytes < (size_t)L.total) return PSFSIM_ERR_WORKSPACE;
 
@@ -63,6 +63,7 @@ int common_build(const float *d_lib, const double *h_radii, int n_r, int n, doub
   h->bstart_off = L.bstart_off;
   h->pts_off = L.pts_off;
   h->status_off = L.status_off;
+  h->libmax_off = L.libmax_off;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = PSFSIM_OK;
   if (cudaGetDevice(&h->device) != cudaSuccess ||
@@ -155,6 +156,10 @@ int psfsim_forward_scratch_bytes(psfsim_t h, int B, size_t *bytes) {
     *bytes = psfsim_forward_fp32_scratch(h, B);
     return PSFSIM_OK;
   }
+  if (h->storage == PSFSIM_SPLIT_BF16) {
+    *bytes = psfsim_forward_tc_scratch(h, B);
+    return PSFSIM_OK;
+  }
   return PSFSIM_ERR_UNSUPPORTED;
 }
 
@@ -162,6 +167,10 @@ int psfsim_adjoint_scratch_bytes(psfsim_t h, int B, size_t *bytes) {
   if (!h || !bytes || B < 1) return PSFSIM_ERR_ARG;
   if (h->storage == PSFSIM_FP32) {
     *bytes = 0;
+    return PSFSIM_OK;
+  }
+  if (h->storage == PSFSIM_SPLIT_BF16) {
+    *bytes = psfsim_adjoint_split_scratch(h, B);
     return PSFSIM_OK;
   }
   return PSFSIM_ERR_UNSUPPORTED;
@@ -177,17 +186,26 @@ int psfsim_forward(psfsim_t h, const float *d_x, int B, float *d_y, void *d_scra
     return psfsim_launch_forward_fp32(h, d_x, B, d_y, d_scratch, st) == cudaSuccess ? PSFSIM_OK
                                                                                     : PSFSIM_ERR_CUDA;
   }
+  if (h->storage == PSFSIM_SPLIT_BF16) {
+    const size_t need = psfsim_forward_tc_scratch(h, B);
+    if (!d_scratch || !aligned(d_scratch, 256) || scratch_bytes < need) return PSFSIM_ERR_WORKSPACE;
+    return psfsim_launch_forward_tc(h, d_x, B, d_y, d_scratch, st) == cudaSuccess ? PSFSIM_OK : PSFSIM_ERR_CUDA;
+  }
   return PSFSIM_ERR_UNSUPPORTED;
 }
 
 int psfsim_adjoint(psfsim_t h, const float *d_g, int B, float *d_gx, void *d_scratch, size_t scratch_bytes,
                    void *stream) {
-  (void)d_scratch;
-  (void)scratch_bytes;
   if (!h || !d_g || !d_gx || B < 1) return PSFSIM_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (h->storage == PSFSIM_FP32)
     return psfsim_launch_adjoint_fp32(h, d_g, B, d_gx, st) == cudaSuccess ? PSFSIM_OK : PSFSIM_ERR_CUDA;
+  if (h->storage == PSFSIM_SPLIT_BF16) {
+    const size_t need = psfsim_adjoint_split_scratch(h, B);
+    if (!d_scratch || !aligned(d_scratch, 256) || scratch_bytes < need) return PSFSIM_ERR_WORKSPACE;
+    return psfsim_launch_adjoint_split(h, d_g, B, d_gx, d_scratch, st) == cudaSuccess ? PSFSIM_OK
+                                                                                      : PSFSIM_ERR_CUDA;
+  }
   return PSFSIM_ERR_UNSUPPORTED;
 }
 

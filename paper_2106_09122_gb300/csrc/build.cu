@@ -265,6 +265,7 @@ WsLayout psfsim_layout(int n, int64_t K, int storage, int n_r) {
   L.bstart_off = take((int64_t)(PSFSIM_MAX_RADII + 1) * 4);
   L.pts_off = take(K * 16);
   L.status_off = take(16);
+  L.libmax_off = take(PSFSIM_MAX_RADII * 4);
   L.total = off;
   (void)n_r;
   return L;
@@ -312,6 +313,7 @@ cudaError_t psfsim_launch_build(psfsim_plan *h, cudaStream_t st) {
   bracket_sort_kernel<<<1, 1024, 0, st>>>(geom, h->K, h->n_r, order, bstart);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (h->storage == PSFSIM_FUSED) return cudaSuccess;
+  if (h->storage == PSFSIM_SPLIT_BF16) return psfsim_launch_split_build(h, st);
   if (h->storage != PSFSIM_FP32) return cudaErrorNotSupported;
 
   const int n = h->n;

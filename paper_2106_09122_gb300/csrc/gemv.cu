@@ -235,6 +235,13 @@ cudaError_t psfsim_launch_forward_fp32(const psfsim_plan *h, const float *x, int
   return cudaGetLastError();
 }
 
+cudaError_t psfsim_launch_reduce_partials(const float *part, int KS, int B, int64_t ld, int64_t M, float *y,
+                                          cudaStream_t st) {
+  dim3 grid((unsigned)((ld + kRedRows - 1) / kRedRows), (unsigned)B);
+  fwd_reduce_kernel<<<grid, 256, 0, st>>>(part, KS, B, ld, M, y);
+  return cudaGetLastError();
+}
+
 cudaError_t psfsim_launch_adjoint_fp32(const psfsim_plan *h, const float *g, int B, float *gx, cudaStream_t st) {
   const bool vec = (h->M % 4 == 0) && ((reinterpret_cast<uintptr_t>(g) & 15) == 0);
   cudaError_t e = cudaSuccess;

@@ -32,7 +32,7 @@ struct psfsim_plan {
   double radii[PSFSIM_MAX_RADII];
   char *ws;
   size_t ws_bytes;
-  int64_t a_off, lo_off, scale_off, geom_off, order_off, bstart_off, pts_off, status_off;
+  int64_t a_off, lo_off, scale_off, geom_off, order_off, bstart_off, pts_off, status_off, libmax_off;
   int device, num_sms;
   bool lib_map_ok;
   CUtensorMap lib_map;  // 3D tensor map over the library for TMA staging
@@ -40,7 +40,7 @@ struct psfsim_plan {
 
 // Workspace layout for a given shape; returns total bytes.
 struct WsLayout {
-  int64_t ld, a_off, lo_off, scale_off, geom_off, order_off, bstart_off, pts_off, status_off, total;
+  int64_t ld, a_off, lo_off, scale_off, geom_off, order_off, bstart_off, pts_off, status_off, libmax_off, total;
 };
 WsLayout psfsim_layout(int n, int64_t K, int storage, int n_r);
 
@@ -51,6 +51,17 @@ cudaError_t psfsim_launch_forward_fp32(const psfsim_plan *h, const float *x, int
 size_t psfsim_forward_fp32_scratch(const psfsim_plan *h, int B);
 cudaError_t psfsim_launch_adjoint_fp32(const psfsim_plan *h, const float *g, int B, float *gx,
                                        cudaStream_t st);
+// y[b, i] = sum_ks part[(ks * B + b) * ld + i], fixed order.
+cudaError_t psfsim_launch_reduce_partials(const float *part, int KS, int B, int64_t ld, int64_t M, float *y,
+                                          cudaStream_t st);
+// Split-BF16 storage: build, tensor-core forward, CUDA-core adjoint.
+cudaError_t psfsim_launch_split_build(psfsim_plan *h, cudaStream_t st);
+size_t psfsim_forward_tc_scratch(const psfsim_plan *h, int B);
+cudaError_t psfsim_launch_forward_tc(const psfsim_plan *h, const float *x, int B, float *y, void *scratch,
+                                     cudaStream_t st);
+size_t psfsim_adjoint_split_scratch(const psfsim_plan *h, int B);
+cudaError_t psfsim_launch_adjoint_split(const psfsim_plan *h, const float *g, int B, float *gx, void *scratch,
+                                        cudaStream_t st);
 
 static inline int64_t psfsim_round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 

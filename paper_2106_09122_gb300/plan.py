@@ -126,6 +126,18 @@ class Plan:
         flat = self.workspace[self.info.a_offset:self.info.a_offset + ld * self.K * 4].view(torch.float32)
         return flat.view(self.K, ld)[:, : self.M].t()
 
+    def A_split(self):
+        """(hi [rows, ld] bf16, lo [rows, ld] bf16, scale [ld] f32) views of split-BF16 storage."""
+        if self.info.storage != B.SPLIT_BF16:
+            raise ValueError("A_split needs SPLIT_BF16 storage")
+        ld = self.info.ld
+        rows = (self.M + 127) // 128 * 128
+        nb = rows * ld * 2
+        hi = self.workspace[self.info.a_offset:self.info.a_offset + nb].view(torch.bfloat16).view(rows, ld)
+        lo = self.workspace[self.info.lo_offset:self.info.lo_offset + nb].view(torch.bfloat16).view(rows, ld)
+        sc = self.workspace[self.info.scale_offset:self.info.scale_offset + ld * 4].view(torch.float32)
+        return hi, lo, sc
+
     def free(self) -> None:
         if getattr(self, "handle", None):
             self._lib.psfsim_free(self.handle)
