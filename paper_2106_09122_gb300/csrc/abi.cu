@@ -34,7 +34,8 @@ int common_build(const float *d_lib, const double *h_radii, int n_r, int n, doub
   if (!storage_ok(storage) || (interp != PSFSIM_LINEAR && interp != PSFSIM_NEAREST)) return PSFSIM_ERR_ARG;
   if (!aligned(d_lib, 16)) return PSFSIM_ERR_ARG;
   if (int rc = check_radii(h_radii, n_r)) return rc;
-  if (storage == PSFSIM_FUSED) return PSFSIM_ERR_UNSUPPORTED;
+  // FUSED uses the exact quarter-turn symmetry of an even N x N scene grid.
+  if (storage == PSFSIM_FUSED && (h_xy || N < 2 || (N & 1))) return PSFSIM_ERR_UNSUPPORTED;
   const WsLayout L = psfsim_layout(n, K, storage, n_r);
   if (!aligned(d_ws, 256) || ws_bytes < (size_t)L.total) return PSFSIM_ERR_WORKSPACE;
 
@@ -50,6 +51,8 @@ int common_build(const float *d_lib, const double *h_radii, int n_r, int n, doub
   h->ld = L.ld;
   h->N = N;
   h->S = S;
+  h->quadrant = storage == PSFSIM_FUSED;
+  h->Kg = h->quadrant ? K / 4 : K;
   h->s = s;
   h->d_lib = d_lib;
   for (int i = 0; i < n_r; ++i) h->radii[i] = h_radii[i];
@@ -160,6 +163,10 @@ int psfsim_forward_scratch_bytes(psfsim_t h, int B, size_t *bytes) {
     *bytes = psfsim_forward_tc_scratch(h, B);
     return PSFSIM_OK;
   }
+  if (h->storage == PSFSIM_FUSED) {
+    *bytes = psfsim_forward_fused_scratch(h, B);
+    return PSFSIM_OK;
+  }
   return PSFSIM_ERR_UNSUPPORTED;
 }
 
@@ -190,6 +197,12 @@ int psfsim_forward(psfsim_t h, const float *d_x, int B, float *d_y, void *d_scra
     const size_t need = psfsim_forward_tc_scratch(h, B);
     if (!d_scratch || !aligned(d_scratch, 256) || scratch_bytes < need) return PSFSIM_ERR_WORKSPACE;
     return psfsim_launch_forward_tc(h, d_x, B, d_y, d_scratch, st) == cudaSuccess ? PSFSIM_OK : PSFSIM_ERR_CUDA;
+  }
+  if (h->storage == PSFSIM_FUSED) {
+    const size_t need = psfsim_forward_fused_scratch(h, B);
+    if (!d_scratch || !aligned(d_scratch, 256) || scratch_bytes < need) return PSFSIM_ERR_WORKSPACE;
+    return psfsim_launch_forward_fused(h, d_x, B, d_y, d_scratch, st) == cudaSuccess ? PSFSIM_OK
+                                                                                     : PSFSIM_ERR_CUDA;
   }
   return PSFSIM_ERR_UNSUPPORTED;
 }

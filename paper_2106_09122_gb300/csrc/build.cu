@@ -13,7 +13,7 @@ constexpr double kFix = 1099511627776.0;  // 2^PSFSIM_FRAC_BITS
 static_assert(PSFSIM_FRAC_BITS == 40, "kFix");
 
 struct GeomParams {
-  int n_r, N, interp, pad;
+  int n_r, N, interp, quadrant;
   int64_t K;
   double S;
   const double *pts;
@@ -28,6 +28,12 @@ __global__ void geom_kernel(const __grid_constant__ GeomParams P, ColGeom *geom)
   if (P.pts) {
     x = P.pts[2 * j];
     y = P.pts[2 * j + 1];
+  } else if (P.quadrant) {  // x > 0, y > 0 quadrant of an even N x N grid
+    const int H = P.N / 2;
+    const int iy = H + (int)(j / H), ix = H + (int)(j % H);
+    const double half = 0.5 * (double)(P.N - 1);
+    x = __dmul_rn((double)ix - half, P.S);
+    y = __dmul_rn((double)iy - half, P.S);
   } else {
     const int iy = (int)(j / P.N), ix = (int)(j % P.N);
     const double half = 0.5 * (double)(P.N - 1);
@@ -41,7 +47,11 @@ __global__ void geom_kernel(const __grid_constant__ GeomParams P, ColGeom *geom)
     s = __ddiv_rn(y, r);
   }
   ColGeom g;
-  g.pad = 0;
+  {
+    const float th = atan2f((float)y, (float)x);  // ordering only
+    int bin = (int)((th + 3.14159265f) * (PSFSIM_THETA_BINS / 6.2831853f));
+    g.bin = bin < 0 ? 0 : (bin >= PSFSIM_THETA_BINS ? PSFSIM_THETA_BINS - 1 : bin);
+  }
   g.C = __double2ll_rn(c * kFix);
   g.Sn = __double2ll_rn(s * kFix);
   if (!(r <= P.radii[P.n_r - 1])) {
@@ -64,33 +74,50 @@ __global__ void geom_kernel(const __grid_constant__ GeomParams P, ColGeom *geom)
   geom[j] = g;
 }
 
-// Counting sort of the columns by radial bracket (bucket n_r-1 holds the zero
-// columns) so that a CTA can stage one bracket pair and build many columns.
+__device__ __forceinline__ int column_bucket(const ColGeom &g, int n_r) {
+  return g.k < 0 ? psfsim_num_buckets(n_r) - 1 : g.k * PSFSIM_THETA_BINS + g.bin;
+}
+
+// Stable counting sort of the columns by (radial bracket, angle bin), zero
+// columns last, so that a CTA can stage one bracket pair for many columns and
+// neighbouring columns read nearby library pixels.  The scatter is done by
+// one warp in index order (match_any ranks), so the order is deterministic.
 __global__ void __launch_bounds__(1024) bracket_sort_kernel(const ColGeom *geom, int64_t K, int n_r,
                                                             int *order, int *bstart) {
-  __shared__ int cnt[PSFSIM_MAX_RADII + 1];
-  __shared__ int cur[PSFSIM_MAX_RADII + 1];
-  for (int b = threadIdx.x; b <= n_r; b += blockDim.x) cnt[b] = 0;
+  constexpr int kMaxBuckets = (PSFSIM_MAX_RADII - 1) * PSFSIM_THETA_BINS + 1;
+  __shared__ int cnt[kMaxBuckets];
+  const int nb = psfsim_num_buckets(n_r);
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) cnt[b] = 0;
   __syncthreads();
-  for (int64_t j = threadIdx.x; j < K; j += blockDim.x) {
-    const int k = geom[j].k;
-    atomicAdd(&cnt[k < 0 ? n_r - 1 : k], 1);
-  }
+  for (int64_t j = threadIdx.x; j < K; j += blockDim.x) atomicAdd(&cnt[column_bucket(geom[j], n_r)], 1);
   __syncthreads();
   if (threadIdx.x == 0) {
     int run = 0;
-    for (int b = 0; b < n_r; ++b) {
+    for (int b = 0; b < nb; ++b) {
+      const int c = cnt[b];
       bstart[b] = run;
-      cur[b] = run;
-      run += cnt[b];
+      cnt[b] = run;  // becomes the scatter cursor
+      run += c;
     }
-    bstart[n_r] = run;
+    bstart[nb] = run;
   }
   __syncthreads();
-  for (int64_t j = threadIdx.x; j < K; j += blockDim.x) {
-    const int k = geom[j].k;
-    const int pos = atomicAdd(&cur[k < 0 ? n_r - 1 : k], 1);
-    order[pos] = (int)j;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int64_t base = 0; base < K; base += 32) {
+      const int64_t j = base + lane;
+      const int key = j < K ? column_bucket(geom[j], n_r) : -1;
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      const int leader = __ffs(peers) - 1;
+      int pos0 = 0;
+      if (lane == leader && key >= 0) pos0 = cnt[key];
+      pos0 = __shfl_sync(0xffffffffu, pos0, leader);
+      if (key >= 0) order[pos0 + __popc(peers & lt)] = (int)j;
+      __syncwarp();
+      if (lane == leader && key >= 0) cnt[key] = pos0 + __popc(peers);
+      __syncwarp();
+    }
   }
 }
 
@@ -213,7 +240,7 @@ __global__ void __launch_bounds__(512) build_fp32_kernel(const __grid_constant__
   for (int64_t pos = begin; pos < end;) {
     const int j0 = P.order[pos];
     const int k = P.geom[j0].k;
-    const int bucket = k < 0 ? P.n_r - 1 : k;
+    const int bucket = column_bucket(P.geom[j0], P.n_r);
     const int64_t gend = min(end, (int64_t)P.bstart[bucket + 1]);
     if (kSmem && k >= 0 && k != cur_k) {
       __syncthreads();  // every warp is done with the previous pair
@@ -262,7 +289,7 @@ WsLayout psfsim_layout(int n, int64_t K, int storage, int n_r) {
   }
   L.geom_off = take(K * (int64_t)sizeof(ColGeom));
   L.order_off = take(K * 4);
-  L.bstart_off = take((int64_t)(PSFSIM_MAX_RADII + 1) * 4);
+  L.bstart_off = take((int64_t)(psfsim_num_buckets(PSFSIM_MAX_RADII) + 1) * 4);
   L.pts_off = take(K * 16);
   L.status_off = take(16);
   L.libmax_off = take(PSFSIM_MAX_RADII * 4);
@@ -298,9 +325,10 @@ cudaError_t psfsim_launch_build(psfsim_plan *h, cudaStream_t st) {
   G.n_r = h->n_r;
   G.N = h->N;
   G.interp = h->interp;
-  G.K = h->K;
+  G.K = h->Kg;
   G.S = h->S;
   G.pts = h->N ? nullptr : reinterpret_cast<const double *>(h->ws + h->pts_off);
+  G.quadrant = h->quadrant ? 1 : 0;
   for (int i = 0; i < h->n_r; ++i) G.radii[i] = h->radii[i];
   ColGeom *geom = reinterpret_cast<ColGeom *>(h->ws + h->geom_off);
   int *order = reinterpret_cast<int *>(h->ws + h->order_off);
@@ -308,11 +336,20 @@ cudaError_t psfsim_launch_build(psfsim_plan *h, cudaStream_t st) {
   int *status = reinterpret_cast<int *>(h->ws + h->status_off);
   cudaError_t e = cudaMemsetAsync(status, 0, 16, st);
   if (e != cudaSuccess) return e;
-  geom_kernel<<<(unsigned)((h->K + 255) / 256), 256, 0, st>>>(G, geom);
+  geom_kernel<<<(unsigned)((h->Kg + 255) / 256), 256, 0, st>>>(G, geom);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  bracket_sort_kernel<<<1, 1024, 0, st>>>(geom, h->K, h->n_r, order, bstart);
+  bracket_sort_kernel<<<1, 1024, 0, st>>>(geom, h->Kg, h->n_r, order, bstart);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (h->storage == PSFSIM_FUSED) return cudaSuccess;
+  if (h->storage == PSFSIM_FUSED) {
+    // The host needs the number of columns inside the last radius to size launches.
+    int kv = 0;
+    if ((e = cudaMemcpyAsync(&kv, bstart + psfsim_num_buckets(h->n_r) - 1, sizeof(int), cudaMemcpyDeviceToHost,
+                             st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return e;
+    h->K_valid = kv;
+    return cudaSuccess;
+  }
   if (h->storage == PSFSIM_SPLIT_BF16) return psfsim_launch_split_build(h, st);
   if (h->storage != PSFSIM_FP32) return cudaErrorNotSupported;
 

@@ -9,6 +9,9 @@
 
 #define PSFSIM_MAX_RADII 256
 #define PSFSIM_FRAC_BITS 40  // fixed-point fraction bits of the rotation coordinates
+#define PSFSIM_THETA_BINS 16 // angle bins per radial bracket when ordering columns
+// Column-ordering buckets: (bracket, angle bin) for valid columns, one more for zero columns.
+static inline __host__ __device__ int psfsim_num_buckets(int n_r) { return (n_r - 1) * PSFSIM_THETA_BINS + 1; }
 
 // Per-column geometry, computed once per build on the device (FP64, Sec. 2):
 // radial bracket k (-1: beyond the last radius, zero column), the two lerp
@@ -17,7 +20,7 @@
 // theta = 0 the identity and quarter turns exact permutations.
 struct ColGeom {
   int k;
-  int pad;
+  int bin;        // polar-angle bin (0..PSFSIM_THETA_BINS-1), for column ordering only
   float w0, w1;  // weights of L[k] and L[k+1]
   long long C, Sn;
 };
@@ -27,6 +30,9 @@ struct psfsim_plan {
   int storage, interp, n, n_r;
   int64_t M, K, ld;
   int N;          // scene side for grid builds, 0 for point builds
+  bool quadrant;  // FUSED: columns are the x > 0, y > 0 quadrant of the N x N grid
+  int64_t Kg;     // columns with geometry tables (K, or K/4 for the quadrant)
+  int64_t K_valid;  // FUSED: columns inside the last radius (host copy, read back at build)
   double S, s;
   const float *d_lib;
   double radii[PSFSIM_MAX_RADII];
@@ -60,6 +66,10 @@ size_t psfsim_forward_tc_scratch(const psfsim_plan *h, int B);
 cudaError_t psfsim_launch_forward_tc(const psfsim_plan *h, const float *x, int B, float *y, void *scratch,
                                      cudaStream_t st);
 size_t psfsim_adjoint_split_scratch(const psfsim_plan *h, int B);
+// Fused (A regenerated on chip) forward.
+size_t psfsim_forward_fused_scratch(const psfsim_plan *h, int B);
+cudaError_t psfsim_launch_forward_fused(const psfsim_plan *h, const float *x, int B, float *y, void *scratch,
+                                        cudaStream_t st);
 cudaError_t psfsim_launch_adjoint_split(const psfsim_plan *h, const float *g, int B, float *gx, void *scratch,
                                         cudaStream_t st);
 

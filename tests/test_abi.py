@@ -76,6 +76,10 @@ def test_build_rejects_bad_arguments_before_launch(lib):
     assert h.value is None
 
 
+def test_fused_needs_an_even_scene_grid(lib):
+    assert _build(lib, [0.0, 1.0, 2.0], N=9, storage=B.FUSED)[0] == B.ERR_UNSUPPORTED
+
+
 def test_products_reject_null_handles(lib):
     assert lib.psfsim_forward(None, None, 1, None, None, 0, None) == B.ERR_ARG
     assert lib.psfsim_adjoint(None, None, 1, None, None, 0, None) == B.ERR_ARG
