@@ -76,16 +76,18 @@ typedef struct {
 /* Human-readable name of a status code (static string). */
 const char *psfsim_status_string(int status);
 
-/* Bytes of workspace psfsim_build needs for an n x n library applied to an
- * N x N scene (K = N*N columns) with the given storage.  Sec. 3: A has n^2
- * rows and N^2 columns.  Returns PSFSIM_ERR_ARG for bad sizes. */
-int psfsim_workspace_bytes(int n, int64_t K, int storage, size_t *bytes);
+/* Bytes of workspace psfsim_build needs for an n x n library of n_r PSFs
+ * applied to K columns (K = N*N for a scene grid) with the given storage.
+ * Sec. 3: A has n^2 rows and N^2 columns.  Returns PSFSIM_ERR_ARG for bad sizes. */
+int psfsim_workspace_bytes(int n, int n_r, int64_t K, int storage, size_t *bytes);
 
 /* Build the interpolated PSF library A for a scene grid (Sec. 2, the loop over
  * all N^2 scene pixels; Eq. 4-5).
  *   d_lib       device float32 [n_r][n][n], 16-byte aligned; read during the
- *               build, and kept (by pointer) for FUSED storage, so it must then
- *               outlive the handle.
+ *               build only (FUSED storage keeps its own zero-bordered copy in
+ *               the workspace).  FUSED needs an even N (it uses the exact
+ *               quarter-turn symmetry of the scene grid) and synchronizes the
+ *               stream once.
  *   h_radii     host double [n_r], strictly increasing offsets in lambda/D.
  *   s           PSF pixel scale (lambda/D per pixel).  A depends on s only
  *               through the radii; it is validated (> 0).

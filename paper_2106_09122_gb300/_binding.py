@@ -30,7 +30,7 @@ class Info(ctypes.Structure):
 # name -> (restype, argtypes); every symbol include/*.h declares.
 SIGNATURES = {
     "psfsim_status_string": (ctypes.c_char_p, [i32]),
-    "psfsim_workspace_bytes": (i32, [i32, i64, i32, c_size_p]),
+    "psfsim_workspace_bytes": (i32, [i32, i32, i64, i32, c_size_p]),
     "psfsim_build": (i32, [vp, vp, i32, i32, f64, i32, f64, i32, i32, vp, ctypes.c_size_t, vp,
                            ctypes.POINTER(vp)]),
     "psfsim_build_points": (i32, [vp, vp, i32, i32, f64, vp, i64, i32, i32, vp, ctypes.c_size_t, vp,

@@ -67,6 +67,7 @@ int common_build(const float *d_lib, const double *h_radii, int n_r, int n, doub
   h->pts_off = L.pts_off;
   h->status_off = L.status_off;
   h->libmax_off = L.libmax_off;
+  h->plib_off = L.plib_off;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = PSFSIM_OK;
   if (cudaGetDevice(&h->device) != cudaSuccess ||
@@ -104,9 +105,11 @@ const char *psfsim_status_string(int status) {
   }
 }
 
-int psfsim_workspace_bytes(int n, int64_t K, int storage, size_t *bytes) {
-  if (!bytes || n < 1 || n > 4096 || K < 1 || K > (int64_t)1 << 30 || !storage_ok(storage)) return PSFSIM_ERR_ARG;
-  *bytes = (size_t)psfsim_layout(n, K, storage, 2).total;
+int psfsim_workspace_bytes(int n, int n_r, int64_t K, int storage, size_t *bytes) {
+  if (!bytes || n < 1 || n > 4096 || n_r < 2 || n_r > PSFSIM_MAX_RADII || K < 1 || K > (int64_t)1 << 30 ||
+      !storage_ok(storage))
+    return PSFSIM_ERR_ARG;
+  *bytes = (size_t)psfsim_layout(n, K, storage, n_r).total;
   return PSFSIM_OK;
 }
 

@@ -40,16 +40,40 @@ constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccStride = 256;
 constexpr uint32_t kTileBytes = BM * BK * 2;
 
+// An M-tile is a 16 x 8 block of image pixels (tile row r -> pixel
+// (p0 + r / 16, q0 + r % 16)), so a warp's 32 rows form a 16 x 2 patch and its
+// bilinear taps touch few cache lines.
+constexpr int kBlockQ = 16, kBlockP = 8;
+
 struct FusedParams {
-  int n, N, Bp, B, KS, m_tiles, k_tiles, stages;
-  int64_t M, rows, K0v;
+  int n, N, Bp, B, KS, m_tiles, k_tiles, stages, tiles_q;
+  int64_t M, rows, K0v, psz;  // psz: floats per zero-padded PSF, (n + 2)^2
   uint32_t stage_bytes;
   const ColGeom *geom;
   const int *order;
-  const float *lib;
-  float *part;  // [KS][4][B][rows]
+  const float *plib;  // library with a one-pixel zero border, [n_r][n+2][n+2]
+  float *part;        // [KS][4][B][M]
   int *status;
 };
+
+// Per-column constants of one k-tile, shared by the generator warps: the
+// fixed-point source coordinates of the tile's origin pixel and the steps.
+struct ColEntry {
+  long long A0, B0, C, S;
+  int64_t off;  // offset of L[k] in the padded library, or -1 for padding columns
+  float w0, w1;
+};
+
+__global__ void pad_library_kernel(const float *__restrict__ lib, int n, int n_r, float *__restrict__ plib) {
+  const int np = n + 2;
+  const int64_t total = (int64_t)n_r * np * np;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = t / ((int64_t)np * np);
+    const int rem = (int)(t % ((int64_t)np * np));
+    const int p = rem / np - 1, q = rem % np - 1;
+    plib[t] = (p >= 0 && p < n && q >= 0 && q < n) ? lib[(k * n + p) * n + q] : 0.f;
+  }
+}
 
 // xs[(part * 4Bp + m Bp + b) * ldx + t] = part of x_b at scene pixel R^m(order[t]).
 __global__ void fused_xgather(const float *__restrict__ x, int B, int Bp, int N, int64_t K0v, int64_t ldx,
@@ -78,12 +102,17 @@ __global__ void fused_xgather(const float *__restrict__ x, int B, int Bp, int N,
   }
 }
 
-__device__ __forceinline__ float gen_element(const float *L0, const float *L1, int n, long long a2, long long b2,
-                                             float w0, float w1) {
+// One A element from a column-table entry; (du2, dv2) = twice the pixel's
+// offset from the tile origin.  Taps come from the zero-padded library, so
+// only the whole 2 x 2 footprint needs a range check.
+__device__ __forceinline__ float gen_element(const ColEntry &e, const float *__restrict__ plib, int n, int np,
+                                             int64_t psz, int du2, int dv2) {
   constexpr int kShift = PSFSIM_FRAC_BITS + 1;
+  const long long a2 = e.A0 + e.C * du2 + e.S * dv2;
+  const long long b2 = e.B0 - e.S * du2 + e.C * dv2;
   const int q0 = (int)(a2 >> kShift);
   const int p0 = (int)(b2 >> kShift);
-  if (q0 < -1 || q0 > n - 1 || p0 < -1 || p0 > n - 1) return 0.f;
+  if (e.off < 0 || q0 < -1 || q0 > n - 1 || p0 < -1 || p0 > n - 1) return 0.f;
   const unsigned fa = (unsigned)((unsigned long long)a2 >> (kShift - 32));
   const unsigned fb = (unsigned)((unsigned long long)b2 >> (kShift - 32));
   constexpr float kInv32 = 2.3283064365386963e-10f;
@@ -91,18 +120,14 @@ __device__ __forceinline__ float gen_element(const float *L0, const float *L1, i
   const float wa0 = fa ? __uint2float_rn(0u - fa) * kInv32 : 1.f;
   const float wb1 = __uint2float_rn(fb) * kInv32;
   const float wb0 = fb ? __uint2float_rn(0u - fb) * kInv32 : 1.f;
-  const bool r0 = p0 >= 0, r1 = p0 + 1 < n, c0 = q0 >= 0, c1 = q0 + 1 < n;
-  const int o = p0 * n + q0;
-  const float t00 = (r0 && c0) ? __ldg(L0 + o) : 0.f, t01 = (r0 && c1) ? __ldg(L0 + o + 1) : 0.f;
-  const float t10 = (r1 && c0) ? __ldg(L0 + o + n) : 0.f, t11 = (r1 && c1) ? __ldg(L0 + o + n + 1) : 0.f;
-  const float v0 = wb0 * (wa0 * t00 + wa1 * t01) + wb1 * (wa0 * t10 + wa1 * t11);
+  const float *L0 = plib + e.off + (int64_t)(p0 + 1) * np + (q0 + 1);
+  const float v0 = wb0 * (wa0 * __ldg(L0) + wa1 * __ldg(L0 + 1)) + wb1 * (wa0 * __ldg(L0 + np) + wa1 * __ldg(L0 + np + 1));
   float v1 = 0.f;
-  if (w1 != 0.f) {
-    const float u00 = (r0 && c0) ? __ldg(L1 + o) : 0.f, u01 = (r0 && c1) ? __ldg(L1 + o + 1) : 0.f;
-    const float u10 = (r1 && c0) ? __ldg(L1 + o + n) : 0.f, u11 = (r1 && c1) ? __ldg(L1 + o + n + 1) : 0.f;
-    v1 = wb0 * (wa0 * u00 + wa1 * u01) + wb1 * (wa0 * u10 + wa1 * u11);
+  if (e.w1 != 0.f) {
+    const float *L1 = L0 + psz;
+    v1 = wb0 * (wa0 * __ldg(L1) + wa1 * __ldg(L1 + 1)) + wb1 * (wa0 * __ldg(L1 + np) + wa1 * __ldg(L1 + np + 1));
   }
-  return w0 * v0 + w1 * v1;
+  return e.w0 * v0 + e.w1 * v1;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -128,6 +153,21 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volati
   return ok != 0;
 }
 
+// Named barrier over the generator warps that also ANDs a flag across them,
+// so every generator leaves the pipeline at the same point after a timeout.
+__device__ __forceinline__ bool gen_barrier_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, 1, %2, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(kGenWarps * 32)
+      : "memory");
+  return r != 0;
+}
+
 __device__ __forceinline__ int unit_k0(const FusedParams &P, int ks) { return (int)((int64_t)P.k_tiles * ks / P.KS); }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -137,6 +177,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ __align__(8) uint64_t xfull[kMaxStages], gfull[kMaxStages], empty[kMaxStages], tfull[2], tempty[2];
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
+  __shared__ ColEntry ctab[2][BK];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < P.stages; ++s) {
@@ -227,23 +268,25 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ---- generators (+ accumulator drain) ----
-    const int g = warp - 2;
+    const int g = warp - 2;              // 0..15
+    const int gtid = g * 32 + lane;      // 0..511
     const int quarter = warp & 3;        // TMEM lane quarter this warp may access
-    const int rot = g >> 2;              // rotation m whose accumulator columns this warp drains
+    const int rot = g >> 2;              // rotation whose accumulator columns this warp drains
     const int cgrp = g >> 2;             // 16-column group this warp generates
     const int r = quarter * 32 + lane;   // tile row
-    const int n = P.n;
+    const int n = P.n, np = n + 2;
     const long long h = n - 1;
     const long long base = h << PSFSIM_FRAC_BITS;
+    const int du2 = 2 * (r % kBlockQ), dv2 = 2 * (r / kBlockQ);
     uint32_t it = 0, c = 0;
     bool ok = true;
-    for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
       const int ks = u / P.m_tiles, mt = u % P.m_tiles;
       const int k0 = unit_k0(P, ks), k1 = unit_k0(P, ks + 1);
-      const int64_t i = (int64_t)mt * BM + r;
-      const bool row_ok = i < P.M;
-      const int p = row_ok ? (int)(i / n) : 0, q = row_ok ? (int)(i % n) : 0;
-      const long long uu = 2 * q - h, vv = 2 * p - h;
+      const int po = (mt / P.tiles_q) * kBlockP, qo = (mt % P.tiles_q) * kBlockQ;
+      const int p = po + r / kBlockQ, q = qo + r % kBlockQ;
+      const bool row_ok = p < n && q < n;
+      const long long uo = 2 * qo - h, vo = 2 * po - h;
       float sum[kMaxBp];
 #pragma unroll
       for (int t = 0; t < kMaxBp; ++t) sum[t] = 0.f;
@@ -268,34 +311,53 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
         return true;
       };
-      for (int kc = k0; kc < k1 && ok; kc += kChunk, ++c) {
+      // Every exit from this loop happens right after gen_barrier_and, which
+      // all generator warps reach the same number of times.
+      bool stop = false;
+      for (int kc = k0; kc < k1 && !stop; kc += kChunk, ++c) {
         const int kc1 = min(kc + kChunk, k1);
         for (int kt = kc; kt < kc1; ++kt, ++it) {
+          // Column table for this k-tile (double-buffered; one named barrier per tile).
+          ColEntry *tab = ctab[kt & 1];
+          if (gtid < BK) {
+            const int64_t t = (int64_t)kt * BK + gtid;
+            ColEntry e;
+            e.off = -1;
+            e.A0 = e.B0 = e.C = e.S = 0;
+            e.w0 = e.w1 = 0.f;
+            if (t < P.K0v) {
+              const ColGeom gm = P.geom[P.order[t]];
+              e.C = gm.C;
+              e.S = gm.Sn;
+              e.A0 = base + gm.C * uo + gm.Sn * vo;
+              e.B0 = base - gm.Sn * uo + gm.C * vo;
+              e.off = (int64_t)gm.k * P.psz;
+              e.w0 = gm.w0;
+              e.w1 = gm.w1;
+            }
+            tab[gtid] = e;
+          }
+          if (!gen_barrier_and(ok)) {
+            stop = true;
+            break;
+          }
           const int s = (int)(it % P.stages);
           if (!warp_wait(&empty[s], ((it / P.stages) & 1) ^ 1, &abort_flag, P.status)) {
             ok = false;
-            break;
+            continue;
           }
           uint8_t *st = smem + (size_t)s * P.stage_bytes;
           uint32_t hw[8], lw[8];
 #pragma unroll
           for (int cc = 0; cc < 16; cc += 2) {
-            float v[2] = {0.f, 0.f};
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-              const int64_t t = (int64_t)kt * BK + cgrp * 16 + cc + e;
-              if (row_ok && t < P.K0v) {
-                const ColGeom gm = P.geom[P.order[t]];
-                const float *L0 = P.lib + (int64_t)gm.k * P.M;
-                const long long a2 = base + gm.C * uu + gm.Sn * vv;
-                const long long b2 = base - gm.Sn * uu + gm.C * vv;
-                v[e] = gen_element(L0, L0 + P.M, n, a2, b2, gm.w0, gm.w1);
-              }
+            float v0 = 0.f, v1 = 0.f;
+            if (row_ok) {
+              v0 = gen_element(tab[cgrp * 16 + cc], P.plib, n, np, P.psz, du2, dv2);
+              v1 = gen_element(tab[cgrp * 16 + cc + 1], P.plib, n, np, P.psz, du2, dv2);
             }
-            const uint32_t hp = pack_bf16(v[0], v[1]);
-            const float h0 = __uint_as_float(hp << 16), h1 = __uint_as_float(hp & 0xFFFF0000u);
+            const uint32_t hp = pack_bf16(v0, v1);
             hw[cc >> 1] = hp;
-            lw[cc >> 1] = pack_bf16(v[0] - h0, v[1] - h1);
+            lw[cc >> 1] = pack_bf16(v0 - __uint_as_float(hp << 16), v1 - __uint_as_float(hp & 0xFFFF0000u));
           }
           // 128-byte swizzle: 16-byte chunk index XOR (row % 8) inside each 1024-byte row group.
           const uint32_t row_off = (uint32_t)(r >> 3) * 1024 + (uint32_t)(r & 7) * 128;
@@ -311,16 +373,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           __syncwarp();
           if (lane == 0) ptx::mbar_arrive(&gfull[s]);
         }
-        if (!ok) break;
-        if (kc > k0 && !drain(c - 1)) ok = false;
+        if (!stop && ok && kc > k0 && !drain(c - 1)) ok = false;
       }
-      if (!ok || !drain(c - 1)) break;
+      if (stop) break;
+      if (ok && !drain(c - 1)) ok = false;
+      if (!ok) continue;  // the next unit's first barrier takes every generator out
       if (row_ok) {
         int pp = p, qp = q;  // P^rot: (p, q) -> (q, n-1-p), applied rot times
         for (int t = 0; t < rot; ++t) {
-          const int np = qp;
+          const int nxt = qp;
           qp = n - 1 - pp;
-          pp = np;
+          pp = nxt;
         }
         float *out = P.part + ((int64_t)(ks * 4 + rot) * P.B) * P.rows + (int64_t)pp * n + qp;
 #pragma unroll
@@ -358,7 +421,7 @@ bool encode_x_map(CUtensorMap *map, const void *base, uint64_t inner, uint64_t o
 }
 
 struct FusedPlanInfo {
-  int Bp, KS, m_tiles, k_tiles, stages;
+  int Bp, KS, m_tiles, k_tiles, stages, tiles_q;
   int64_t rows, ldx;
   uint32_t stage_bytes;
   size_t smem, xs_bytes, part_bytes;
@@ -368,7 +431,8 @@ FusedPlanInfo fused_info(const psfsim_plan *h, int Bc) {
   FusedPlanInfo f;
   f.Bp = Bc <= 16 ? 16 : 32;
   f.rows = psfsim_round_up(h->M, BM);
-  f.m_tiles = (int)(f.rows / BM);
+  f.tiles_q = (h->n + kBlockQ - 1) / kBlockQ;
+  f.m_tiles = f.tiles_q * ((h->n + kBlockP - 1) / kBlockP);
   f.k_tiles = (int)((h->K_valid + BK - 1) / BK);
   if (f.k_tiles < 1) f.k_tiles = 1;
   f.ldx = (int64_t)f.k_tiles * BK;
@@ -384,6 +448,12 @@ FusedPlanInfo fused_info(const psfsim_plan *h, int Bc) {
 }
 
 }  // namespace
+
+cudaError_t psfsim_launch_pad_library(psfsim_plan *h, cudaStream_t st) {
+  pad_library_kernel<<<h->num_sms * 4, 256, 0, st>>>(h->d_lib, h->n, h->n_r,
+                                                     reinterpret_cast<float *>(h->ws + h->plib_off));
+  return cudaGetLastError();
+}
 
 size_t psfsim_forward_fused_scratch(const psfsim_plan *h, int B) {
   const int Bc = B < kMaxBp ? B : kMaxBp;
@@ -414,6 +484,8 @@ cudaError_t psfsim_launch_forward_fused(const psfsim_plan *h, const float *x, in
     P.B = Bc;
     P.KS = f.KS;
     P.m_tiles = f.m_tiles;
+    P.tiles_q = f.tiles_q;
+    P.psz = (int64_t)(h->n + 2) * (h->n + 2);
     P.k_tiles = f.k_tiles;
     P.stages = f.stages;
     P.M = h->M;
@@ -422,7 +494,7 @@ cudaError_t psfsim_launch_forward_fused(const psfsim_plan *h, const float *x, in
     P.stage_bytes = f.stage_bytes;
     P.geom = reinterpret_cast<const ColGeom *>(h->ws + h->geom_off);
     P.order = order;
-    P.lib = h->d_lib;
+    P.plib = reinterpret_cast<const float *>(h->ws + h->plib_off);
     P.part = part;
     P.status = status;
     if ((e = cudaFuncSetAttribute(fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem)) !=

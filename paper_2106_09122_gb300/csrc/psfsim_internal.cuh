@@ -38,7 +38,7 @@ struct psfsim_plan {
   double radii[PSFSIM_MAX_RADII];
   char *ws;
   size_t ws_bytes;
-  int64_t a_off, lo_off, scale_off, geom_off, order_off, bstart_off, pts_off, status_off, libmax_off;
+  int64_t a_off, lo_off, scale_off, geom_off, order_off, bstart_off, pts_off, status_off, libmax_off, plib_off;
   int device, num_sms;
   bool lib_map_ok;
   CUtensorMap lib_map;  // 3D tensor map over the library for TMA staging
@@ -46,9 +46,10 @@ struct psfsim_plan {
 
 // Workspace layout for a given shape; returns total bytes.
 struct WsLayout {
-  int64_t ld, a_off, lo_off, scale_off, geom_off, order_off, bstart_off, pts_off, status_off, libmax_off, total;
+  int64_t ld, a_off, lo_off, scale_off, geom_off, order_off, bstart_off, pts_off, status_off, libmax_off, plib_off, total;
 };
 WsLayout psfsim_layout(int n, int64_t K, int storage, int n_r);
+cudaError_t psfsim_launch_pad_library(psfsim_plan *h, cudaStream_t st);
 
 // Kernel launchers (return cudaError_t of the launch).
 cudaError_t psfsim_launch_build(psfsim_plan *h, cudaStream_t st);

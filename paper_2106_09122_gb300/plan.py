@@ -27,9 +27,9 @@ def _dev_f32(t: torch.Tensor, name: str) -> torch.Tensor:
     return t
 
 
-def workspace_bytes(n: int, K: int, storage: str = "fp32") -> int:
+def workspace_bytes(n: int, n_r: int, K: int, storage: str = "fp32") -> int:
     out = ctypes.c_size_t()
-    B.check(B.load().psfsim_workspace_bytes(n, K, _STORAGE[storage], ctypes.byref(out)), "workspace_bytes")
+    B.check(B.load().psfsim_workspace_bytes(n, n_r, K, _STORAGE[storage], ctypes.byref(out)), "workspace_bytes")
     return out.value
 
 
@@ -51,7 +51,7 @@ class Plan:
         else:
             K = int(N) * int(N)
         self.K, self.M = K, self.n * self.n
-        ws = workspace_bytes(self.n, K, storage)
+        ws = workspace_bytes(self.n, self.n_r, K, storage)
         self.workspace = torch.empty(ws, dtype=torch.uint8, device=lib.device)
         h = ctypes.c_void_p()
         rp = self.radii.ctypes.data_as(ctypes.c_void_p)

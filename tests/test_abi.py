@@ -46,11 +46,16 @@ def test_status_strings(lib):
 
 def test_workspace_bytes_covers_A(lib):
     out = ctypes.c_size_t()
-    assert lib.psfsim_workspace_bytes(128, 128 * 128, B.FP32, ctypes.byref(out)) == B.OK
+    assert lib.psfsim_workspace_bytes(128, 40, 128 * 128, B.FP32, ctypes.byref(out)) == B.OK
     assert out.value >= 128 * 128 * 128 * 128 * 4
-    assert lib.psfsim_workspace_bytes(0, 10, B.FP32, ctypes.byref(out)) == B.ERR_ARG
-    assert lib.psfsim_workspace_bytes(16, 10, 7, ctypes.byref(out)) == B.ERR_ARG
-    assert lib.psfsim_workspace_bytes(16, 10, B.FP32, None) == B.ERR_ARG
+    assert lib.psfsim_workspace_bytes(128, 40, 128 * 128, B.SPLIT_BF16, ctypes.byref(out)) == B.OK
+    assert out.value >= 2 * 2 * 128 * 128 * 128 * 128
+    assert lib.psfsim_workspace_bytes(512, 80, 512 * 512, B.FUSED, ctypes.byref(out)) == B.OK
+    assert 80 * 514 * 514 * 4 <= out.value < 200 * 2 ** 20
+    assert lib.psfsim_workspace_bytes(0, 4, 10, B.FP32, ctypes.byref(out)) == B.ERR_ARG
+    assert lib.psfsim_workspace_bytes(16, 1, 10, B.FP32, ctypes.byref(out)) == B.ERR_ARG
+    assert lib.psfsim_workspace_bytes(16, 4, 10, 7, ctypes.byref(out)) == B.ERR_ARG
+    assert lib.psfsim_workspace_bytes(16, 4, 10, B.FP32, None) == B.ERR_ARG
 
 
 def _build(lib, radii, lib_ptr=0x1000, ws_ptr=0x100000, ws_bytes=1 << 40, n=16, N=8, storage=B.FP32):
