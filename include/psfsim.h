@@ -122,6 +122,38 @@ int psfsim_adjoint_scratch_bytes(psfsim_t h, int B, size_t *bytes);
 int psfsim_forward(psfsim_t h, const float *d_x, int B, float *d_y, void *d_scratch,
                    size_t scratch_bytes, void *stream);
 
+/* One product of a multi-job launch: S = A Z for up to 80 scenes of one
+ * SPLIT_BF16 plan.  d_count (device int, may be NULL) holds how many of the
+ * `capacity` scene slots are present in this call, so a captured CUDA graph
+ * can be replayed for batches of different composition; slots at and beyond
+ * *d_count are neither read nor written. */
+typedef struct {
+  psfsim_t plan;
+  const float *d_x;   /* device float32 [capacity][K] */
+  float *d_y;         /* device float32 [capacity][M] */
+  int capacity;       /* 1..80 */
+  const int *d_count; /* device int, or NULL for all `capacity` scenes */
+} psfsim_job_t;
+
+/* Launch-shape knobs of the tensor-core forward (0 = default): k-tiles (of 64)
+ * accumulated in TMEM between drains (1..8), target work units per SM, and
+ * shared-memory pipeline stages (2..8). */
+typedef struct {
+  int chunk;
+  int units_per_sm;
+  int stages;
+} psfsim_tuning_t;
+
+/* Batched S_j = A_j Z_j (Eq. 6) for several SPLIT_BF16 plans at once — e.g.
+ * scenes of different sizes and pixel scales, each with its own A — in one
+ * persistent tensor-core launch whose work units interleave all jobs (plus one
+ * split and one reduction launch per job).  1 <= njobs <= 16, all plans on
+ * the current device.  `tuning` may be NULL.  Deterministic. */
+int psfsim_forward_multi_scratch_bytes(const psfsim_job_t *jobs, int njobs, const psfsim_tuning_t *tuning,
+                                       size_t *bytes);
+int psfsim_forward_multi(const psfsim_job_t *jobs, int njobs, const psfsim_tuning_t *tuning, void *d_scratch,
+                         size_t scratch_bytes, void *stream);
+
 /* Capacity of the fixed device array psfsim_forward_static works in. */
 #define PSFSIM_STATIC_SCRATCH_BYTES ((size_t)16 * 1024 * 1024)
 

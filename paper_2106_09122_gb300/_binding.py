@@ -27,6 +27,14 @@ class Info(ctypes.Structure):
                 ("lo_offset", i64), ("scale_offset", i64), ("workspace_bytes", i64)]
 
 
+class Job(ctypes.Structure):
+    _fields_ = [("plan", vp), ("d_x", vp), ("d_y", vp), ("capacity", i32), ("d_count", vp)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("chunk", i32), ("units_per_sm", i32), ("stages", i32)]
+
+
 # name -> (restype, argtypes); every symbol include/*.h declares.
 SIGNATURES = {
     "psfsim_status_string": (ctypes.c_char_p, [i32]),
@@ -41,6 +49,8 @@ SIGNATURES = {
     "psfsim_forward": (i32, [vp, vp, i32, vp, vp, ctypes.c_size_t, vp]),
     "psfsim_adjoint": (i32, [vp, vp, i32, vp, vp, ctypes.c_size_t, vp]),
     "psfsim_forward_static": (i32, [vp, vp, i32, vp, vp]),
+    "psfsim_forward_multi_scratch_bytes": (i32, [ctypes.POINTER(Job), i32, ctypes.POINTER(Tuning), c_size_p]),
+    "psfsim_forward_multi": (i32, [ctypes.POINTER(Job), i32, ctypes.POINTER(Tuning), vp, ctypes.c_size_t, vp]),
     "psfsim_sync_status": (i32, [vp, vp]),
     "psfsim_ring_chain_scratch_bytes": (i32, [i32, c_size_p]),
     "psfsim_loss_scratch_bytes": (i32, [i64, c_size_p]),

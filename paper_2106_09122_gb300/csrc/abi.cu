@@ -225,6 +225,24 @@ int psfsim_adjoint(psfsim_t h, const float *d_g, int B, float *d_gx, void *d_scr
   return PSFSIM_ERR_UNSUPPORTED;
 }
 
+int psfsim_forward_multi_scratch_bytes(const psfsim_job_t *jobs, int njobs, const psfsim_tuning_t *tuning,
+                                       size_t *bytes) {
+  if (!bytes) return PSFSIM_ERR_ARG;
+  if (int rc = psfsim_multi_validate(jobs, njobs)) return rc;
+  *bytes = psfsim_forward_multi_scratch(jobs, njobs, tuning);
+  return PSFSIM_OK;
+}
+
+int psfsim_forward_multi(const psfsim_job_t *jobs, int njobs, const psfsim_tuning_t *tuning, void *d_scratch,
+                         size_t scratch_bytes, void *stream) {
+  if (int rc = psfsim_multi_validate(jobs, njobs)) return rc;
+  if (!d_scratch || !aligned(d_scratch, 256) || scratch_bytes < psfsim_forward_multi_scratch(jobs, njobs, tuning))
+    return PSFSIM_ERR_WORKSPACE;
+  return psfsim_launch_forward_multi(jobs, njobs, tuning, d_scratch, static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? PSFSIM_OK
+             : PSFSIM_ERR_CUDA;
+}
+
 int psfsim_sync_status(psfsim_t h, void *stream) {
   if (!h) return PSFSIM_ERR_ARG;
   if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return PSFSIM_ERR_CUDA;

@@ -503,7 +503,7 @@ cudaError_t psfsim_launch_forward_fused(const psfsim_plan *h, const float *x, in
     const int units = f.m_tiles * f.KS;
     fused_kernel<<<units < h->num_sms ? units : h->num_sms, kThreads, f.smem, st>>>(mx, P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = psfsim_launch_reduce_partials(part, 4 * f.KS, Bc, f.rows, h->M, y + (int64_t)b0 * h->M, st)) !=
+    if ((e = psfsim_launch_reduce_partials(part, 4 * f.KS, Bc, f.rows, h->M, y + (int64_t)b0 * h->M, nullptr, st)) !=
         cudaSuccess)
       return e;
   }

@@ -72,11 +72,13 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_partial_kernel(const float *_
 // through shared memory, so every output needs only ~KS/8 loads per thread.
 constexpr int kRedRows = 128;
 __global__ void __launch_bounds__(256) fwd_reduce_kernel(const float *__restrict__ part, int KS, int B,
-                                                         int64_t ld, int64_t M, float *__restrict__ y) {
+                                                         int64_t ld, int64_t M, float *__restrict__ y,
+                                                         const int *__restrict__ count) {
   __shared__ float4 red[8][32];
   const int c4 = threadIdx.x & 31, grp = threadIdx.x >> 5;
   const int64_t r = ((int64_t)blockIdx.x * 32 + c4) * 4;
   const int b = blockIdx.y;
+  if (count && b >= *count) return;  // scene slot not present in this call
   float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
   if (r < ld) {
     const float *p = part + (int64_t)b * ld + r;
@@ -231,14 +233,14 @@ cudaError_t psfsim_launch_forward_fp32(const psfsim_plan *h, const float *x, int
   }
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)((h->ld + kRedRows - 1) / kRedRows), (unsigned)B);
-  fwd_reduce_kernel<<<grid, 256, 0, st>>>(part, KS, B, h->ld, h->M, y);
+  fwd_reduce_kernel<<<grid, 256, 0, st>>>(part, KS, B, h->ld, h->M, y, nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t psfsim_launch_reduce_partials(const float *part, int KS, int B, int64_t ld, int64_t M, float *y,
-                                          cudaStream_t st) {
+                                          const int *count, cudaStream_t st) {
   dim3 grid((unsigned)((ld + kRedRows - 1) / kRedRows), (unsigned)B);
-  fwd_reduce_kernel<<<grid, 256, 0, st>>>(part, KS, B, ld, M, y);
+  fwd_reduce_kernel<<<grid, 256, 0, st>>>(part, KS, B, ld, M, y, count);
   return cudaGetLastError();
 }
 

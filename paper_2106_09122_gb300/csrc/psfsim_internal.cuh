@@ -59,14 +59,20 @@ size_t psfsim_forward_fp32_scratch(const psfsim_plan *h, int B);
 cudaError_t psfsim_launch_adjoint_fp32(const psfsim_plan *h, const float *g, int B, float *gx,
                                        cudaStream_t st);
 // y[b, i] = sum_ks part[(ks * B + b) * ld + i], fixed order.
+// Slots b >= *count (when count is not NULL) are skipped.
 cudaError_t psfsim_launch_reduce_partials(const float *part, int KS, int B, int64_t ld, int64_t M, float *y,
-                                          cudaStream_t st);
+                                          const int *count, cudaStream_t st);
 // Split-BF16 storage: build, tensor-core forward, CUDA-core adjoint.
 cudaError_t psfsim_launch_split_build(psfsim_plan *h, cudaStream_t st);
 size_t psfsim_forward_tc_scratch(const psfsim_plan *h, int B);
 cudaError_t psfsim_launch_forward_tc(const psfsim_plan *h, const float *x, int B, float *y, void *scratch,
                                      cudaStream_t st);
 size_t psfsim_adjoint_split_scratch(const psfsim_plan *h, int B);
+// Multi-job persistent tensor-core forward (several split-BF16 plans, one launch).
+int psfsim_multi_validate(const psfsim_job_t *jobs, int njobs);
+size_t psfsim_forward_multi_scratch(const psfsim_job_t *jobs, int njobs, const psfsim_tuning_t *tune);
+cudaError_t psfsim_launch_forward_multi(const psfsim_job_t *jobs, int njobs, const psfsim_tuning_t *tune,
+                                        void *scratch, cudaStream_t st);
 // Fused (A regenerated on chip) forward.
 size_t psfsim_forward_fused_scratch(const psfsim_plan *h, int B);
 cudaError_t psfsim_launch_forward_fused(const psfsim_plan *h, const float *x, int B, float *y, void *scratch,

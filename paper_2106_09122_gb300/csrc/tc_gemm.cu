@@ -33,25 +33,37 @@ constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccStride = 256;  // TMEM column offset of the second accumulator
 constexpr uint32_t kTileBytes = BM * BK * 2;
 constexpr int kMaxBp = 80;       // 3 * Bp <= 256 (MMA N and TMA box limits), Bp % 16 == 0
-constexpr int kChunkTiles = 4;   // k-tiles (of 64) per TMEM accumulation
+constexpr int kMaxJobs = 16;
+constexpr int kDefaultChunk = 4; // k-tiles (of 64) per TMEM accumulation
+constexpr int kMaxChunk = 8;     // <= 64 accumulating MMAs between drains
 
-struct TcParams {
-  int64_t rows;  // M rounded up to 128
-  int64_t M;
-  int B, Bp, KS, m_tiles, k_tiles, stages;
-  int chunk;     // k-tiles accumulated in TMEM before the epilogue drains them
+// One product S_j = A_j Z_j of a (possibly multi-job) launch.
+struct TcJob {
+  int64_t rows, M;
+  int Bp, KS, m_tiles, k_tiles;
+  int unit_begin;      // first work unit of this job
+  int cap;             // scenes in the job's buffers (<= Bp)
+  const int *count;    // device int: scenes present (NULL: all cap)
+  float *part;         // [KS][cap][rows]
+};
+
+// Kernel parameter block: tensor maps (hi, lo, x) and geometry of every job.
+struct TcMulti {
+  CUtensorMap map[kMaxJobs][3];
+  TcJob job[kMaxJobs];
+  int njobs, units, stages, chunk;
   uint32_t stage_bytes;
-  float *part;   // [KS][B][rows]
   int *status;
 };
 
-__global__ void xsplit_kernel(const float *__restrict__ x, int B, int Bp, int64_t K, int64_t ld,
-                              const float *__restrict__ scale, __nv_bfloat16 *__restrict__ xs) {
+__global__ void xsplit_kernel(const float *__restrict__ x, int B, const int *__restrict__ count, int Bp, int64_t K,
+                              int64_t ld, const float *__restrict__ scale, __nv_bfloat16 *__restrict__ xs) {
   const int64_t total = (int64_t)Bp * ld;
+  const int nb = count ? min(*count, B) : B;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int b = (int)(t / ld);
     const int64_t j = t % ld;
-    const float v = (b < B && j < K) ? x[(int64_t)b * K + j] * scale[j] : 0.f;
+    const float v = (b < nb && j < K) ? x[(int64_t)b * K + j] * scale[j] : 0.f;
     const __nv_bfloat16 x1 = __float2bfloat16_rn(v);
     const float r1 = v - __bfloat162float(x1);
     const __nv_bfloat16 x2 = __float2bfloat16_rn(r1);
@@ -67,9 +79,15 @@ __device__ __forceinline__ void set_abort(volatile int *abort_flag, int *status)
   atomicExch(status, PSFSIM_ERR_TIMEOUT);
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
-                   const __grid_constant__ CUtensorMap map_x, const TcParams P) {
+__device__ __forceinline__ int find_job(const TcMulti &P, int u) {
+  int j = 0;
+  while (j + 1 < P.njobs && u >= P.job[j + 1].unit_begin) ++j;
+  return j;
+}
+
+__device__ __forceinline__ int k_begin(const TcJob &J, int ks) { return (int)((int64_t)J.k_tiles * ks / J.KS); }
+
+__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcMulti P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], tfull_bar[2], tempty_bar[2];
@@ -88,9 +106,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     abort_flag = 0;
     ptx::fence_mbar_init();
-    ptx::prefetch_tensormap(&map_hi);
-    ptx::prefetch_tensormap(&map_lo);
-    ptx::prefetch_tensormap(&map_x);
   }
   if (warp == 0) {
     ptx::tmem_alloc(&tmem_base_sh, kTmemCols);
@@ -100,38 +115,41 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tbase = tmem_base_sh;
-  const int units = P.m_tiles * P.KS;
-  const int Bp = P.Bp;
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
     uint32_t it = 0;
-    const uint32_t tx = 2 * kTileBytes + (uint32_t)(3 * Bp) * BK * 2;
-    for (int u = blockIdx.x; u < units && !abort_flag; u += gridDim.x) {
-      const int ks = u / P.m_tiles, mt = u % P.m_tiles;
-      const int k0 = (int)((int64_t)P.k_tiles * ks / P.KS), k1 = (int)((int64_t)P.k_tiles * (ks + 1) / P.KS);
-      for (int kt = k0; kt < k1; ++kt, ++it) {
+    bool ok = true;
+    for (int u = blockIdx.x; u < P.units && ok && !abort_flag; u += gridDim.x) {
+      const int jb = find_job(P, u);
+      const TcJob &J = P.job[jb];
+      const int lu = u - J.unit_begin;
+      const int ks = lu / J.m_tiles, mt = lu % J.m_tiles;
+      const uint32_t tx = 2 * kTileBytes + (uint32_t)(3 * J.Bp) * BK * 2;
+      for (int kt = k_begin(J, ks); kt < k_begin(J, ks + 1); ++kt, ++it) {
         const int s = (int)(it % P.stages);
         if (!ptx::mbar_wait_bounded(&empty_bar[s], ((it / P.stages) & 1) ^ 1)) {
           set_abort(&abort_flag, P.status);
+          ok = false;
           break;
         }
         uint8_t *st = smem + (size_t)s * P.stage_bytes;
         ptx::mbar_arrive_expect_tx(&full_bar[s], tx);
-        ptx::tma_load_2d(st, &map_hi, kt * BK, mt * BM, &full_bar[s]);
-        ptx::tma_load_2d(st + kTileBytes, &map_lo, kt * BK, mt * BM, &full_bar[s]);
-        ptx::tma_load_2d(st + 2 * kTileBytes, &map_x, kt * BK, 0, &full_bar[s]);
+        ptx::tma_load_2d(st, &P.map[jb][0], kt * BK, mt * BM, &full_bar[s]);
+        ptx::tma_load_2d(st + kTileBytes, &P.map[jb][1], kt * BK, mt * BM, &full_bar[s]);
+        ptx::tma_load_2d(st + 2 * kTileBytes, &P.map[jb][2], kt * BK, 0, &full_bar[s]);
       }
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
-    const uint32_t idesc3 = ptx::idesc_bf16_f32(BM, 3 * Bp);
-    const uint32_t idesc2 = ptx::idesc_bf16_f32(BM, 2 * Bp);
     uint32_t it = 0, c = 0;
     bool ok = true;
-    for (int u = blockIdx.x; u < units && ok && !abort_flag; u += gridDim.x) {
-      const int ks = u / P.m_tiles;
-      const int k0 = (int)((int64_t)P.k_tiles * ks / P.KS), k1 = (int)((int64_t)P.k_tiles * (ks + 1) / P.KS);
+    for (int u = blockIdx.x; u < P.units && ok && !abort_flag; u += gridDim.x) {
+      const TcJob &J = P.job[find_job(P, u)];
+      const int ks = (u - J.unit_begin) / J.m_tiles;
+      const int k0 = k_begin(J, ks), k1 = k_begin(J, ks + 1);
+      const uint32_t idesc3 = ptx::idesc_bf16_f32(BM, 3 * J.Bp);
+      const uint32_t idesc2 = ptx::idesc_bf16_f32(BM, 2 * J.Bp);
       for (int kc = k0; kc < k1 && ok; kc += P.chunk, ++c) {
         const int kc1 = min(kc + P.chunk, k1);
         const uint32_t acc = c & 1;
@@ -175,9 +193,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int row = quarter * 32 + lane;
     uint32_t c = 0;
     bool ok = true;
-    for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
-      const int ks = u / P.m_tiles, mt = u % P.m_tiles;
-      const int k0 = (int)((int64_t)P.k_tiles * ks / P.KS), k1 = (int)((int64_t)P.k_tiles * (ks + 1) / P.KS);
+    for (int u = blockIdx.x; u < P.units && ok; u += gridDim.x) {
+      const TcJob &J = P.job[find_job(P, u)];
+      const int lu = u - J.unit_begin;
+      const int ks = lu / J.m_tiles, mt = lu % J.m_tiles;
+      const int k0 = k_begin(J, ks), k1 = k_begin(J, ks + 1);
+      const int Bp = J.Bp;
       float sum[kMaxBp];
 #pragma unroll
       for (int t = 0; t < kMaxBp; ++t) sum[t] = 0.f;
@@ -216,10 +237,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) ptx::mbar_arrive(&tempty_bar[acc]);
       }
       if (!ok) break;
-      float *out = P.part + (int64_t)ks * P.B * P.rows + (int64_t)mt * BM + row;
+      const int nb = J.count ? min(*J.count, J.cap) : J.cap;
+      float *out = J.part + (int64_t)ks * J.cap * J.rows + (int64_t)mt * BM + row;
 #pragma unroll
       for (int t = 0; t < kMaxBp; ++t)
-        if (t < P.B) out[(int64_t)t * P.rows] = sum[t];
+        if (t < nb) out[(int64_t)t * J.rows] = sum[t];
     }
   }
   __syncthreads();
@@ -275,75 +297,171 @@ int choose_ks(int m_tiles, int k_tiles, int num_sms) {
   return best;
 }
 
-struct Chunking {
-  int Bp, KS, m_tiles, k_tiles, stages;
-  uint32_t stage_bytes;
-  size_t smem, xs_bytes, part_bytes;
+struct JobSpec {
+  const psfsim_plan *h;
+  const float *x;
+  float *y;
+  int cap;
+  const int *count;
 };
 
-Chunking plan_chunk(const psfsim_plan *h, int Bc) {
-  Chunking c;
-  c.Bp = (int)psfsim_round_up(Bc, 16);
-  c.m_tiles = (int)(psfsim_round_up(h->M, BM) / BM);
-  c.k_tiles = (int)(h->ld / BK);
-  c.KS = choose_ks(c.m_tiles, c.k_tiles, h->num_sms);
-  c.stage_bytes = (uint32_t)psfsim_round_up(2 * kTileBytes + 3 * c.Bp * BK * 2, 1024);
-  c.stages = (int)((220 * 1024) / c.stage_bytes);
-  if (c.stages > kMaxStages) c.stages = kMaxStages;
-  c.smem = (size_t)c.stages * c.stage_bytes + 1024;
-  c.xs_bytes = (size_t)psfsim_round_up(3ll * c.Bp * h->ld * 2, 256);
-  c.part_bytes = (size_t)c.KS * Bc * psfsim_round_up(h->M, BM) * 4;
-  return c;
+struct JobPlan {
+  int Bp, KS, m_tiles, k_tiles;
+  int64_t rows;
+  size_t xs_off, part_off;
+};
+
+struct MultiPlan {
+  JobPlan jp[kMaxJobs];
+  int njobs, units, stages, chunk;
+  uint32_t stage_bytes;
+  size_t smem, scratch;
+};
+
+// Tile/launch shape of a multi-job product.  `tune` fields of 0 take defaults:
+// chunk = kDefaultChunk k-tiles per TMEM accumulation; split factors chosen so
+// that the whole launch has about units_per_sm work units per SM (or, for a
+// single job without tuning, the smallest split that fills the SMs evenly);
+// as many smem stages as fit.
+MultiPlan plan_multi(const JobSpec *jobs, int nj, const psfsim_tuning_t *tune) {
+  MultiPlan mp;
+  std::memset(&mp, 0, sizeof(mp));
+  mp.njobs = nj;
+  const int num_sms = jobs[0].h->num_sms;
+  const int ups = tune && tune->units_per_sm > 0 ? tune->units_per_sm : 0;
+  int64_t total = 0;
+  for (int j = 0; j < nj; ++j) {
+    const psfsim_plan *h = jobs[j].h;
+    JobPlan &p = mp.jp[j];
+    p.Bp = (int)psfsim_round_up(jobs[j].cap, 16);
+    p.rows = psfsim_round_up(h->M, BM);
+    p.m_tiles = (int)(p.rows / BM);
+    p.k_tiles = (int)(h->ld / BK);
+    total += (int64_t)p.m_tiles * p.k_tiles;
+  }
+  const int64_t target_units = (int64_t)(ups ? ups : 4) * num_sms;
+  const int64_t per_unit = (total + target_units - 1) / target_units;
+  int Bp_max = 16, units = 0;
+  size_t off = 0;
+  for (int j = 0; j < nj; ++j) {
+    JobPlan &p = mp.jp[j];
+    if (nj == 1 && !ups) {
+      p.KS = choose_ks(p.m_tiles, p.k_tiles, num_sms);
+    } else {
+      int ks = (int)((p.k_tiles + per_unit - 1) / (per_unit > 0 ? per_unit : 1));
+      ks = ks < 1 ? 1 : ks;
+      ks = ks > 64 ? 64 : ks;
+      p.KS = ks > p.k_tiles ? p.k_tiles : ks;
+    }
+    units += p.m_tiles * p.KS;
+    Bp_max = p.Bp > Bp_max ? p.Bp : Bp_max;
+    const psfsim_plan *h = jobs[j].h;
+    p.xs_off = off;
+    off += (size_t)psfsim_round_up(3ll * p.Bp * h->ld * 2, 256);
+    p.part_off = off;
+    off += (size_t)psfsim_round_up((int64_t)p.KS * jobs[j].cap * p.rows * 4, 256);
+  }
+  mp.units = units;
+  mp.scratch = off;
+  mp.stage_bytes = (uint32_t)psfsim_round_up(2 * kTileBytes + 3 * Bp_max * BK * 2, 1024);
+  int fit = (int)((220 * 1024) / mp.stage_bytes);
+  fit = fit > kMaxStages ? kMaxStages : fit;
+  mp.stages = tune && tune->stages >= 2 && tune->stages < fit ? tune->stages : fit;
+  mp.chunk = tune && tune->chunk > 0 ? (tune->chunk > kMaxChunk ? kMaxChunk : tune->chunk) : kDefaultChunk;
+  mp.smem = (size_t)mp.stages * mp.stage_bytes + 1024;
+  return mp;
+}
+
+cudaError_t launch_multi(const JobSpec *jobs, int nj, const MultiPlan &mp, void *scratch, cudaStream_t st) {
+  char *base = static_cast<char *>(scratch);
+  cudaError_t e;
+  TcMulti P;  // kernel parameter block, copied at launch
+  std::memset(&P, 0, sizeof(P));
+  for (int j = 0; j < nj; ++j) {
+    const psfsim_plan *h = jobs[j].h;
+    const JobPlan &p = mp.jp[j];
+    __nv_bfloat16 *xs = reinterpret_cast<__nv_bfloat16 *>(base + p.xs_off);
+    const float *scale = reinterpret_cast<const float *>(h->ws + h->scale_off);
+    xsplit_kernel<<<h->num_sms * 4, 256, 0, st>>>(jobs[j].x, jobs[j].cap, jobs[j].count, p.Bp, h->K, h->ld, scale,
+                                                  xs);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (!encode_bf16_2d(&P.map[j][0], h->ws + h->a_off, (uint64_t)h->ld, (uint64_t)p.rows, BK, BM) ||
+        !encode_bf16_2d(&P.map[j][1], h->ws + h->lo_off, (uint64_t)h->ld, (uint64_t)p.rows, BK, BM) ||
+        !encode_bf16_2d(&P.map[j][2], xs, (uint64_t)h->ld, (uint64_t)(3 * p.Bp), BK, (uint32_t)(3 * p.Bp)))
+      return cudaErrorInvalidValue;
+    TcJob &J = P.job[j];
+    J.rows = p.rows;
+    J.M = h->M;
+    J.Bp = p.Bp;
+    J.KS = p.KS;
+    J.m_tiles = p.m_tiles;
+    J.k_tiles = p.k_tiles;
+    J.unit_begin = j == 0 ? 0 : P.job[j - 1].unit_begin + P.job[j - 1].m_tiles * P.job[j - 1].KS;
+    J.cap = jobs[j].cap;
+    J.count = jobs[j].count;
+    J.part = reinterpret_cast<float *>(base + p.part_off);
+  }
+  P.njobs = nj;
+  P.units = mp.units;
+  P.stages = mp.stages;
+  P.chunk = mp.chunk;
+  P.stage_bytes = mp.stage_bytes;
+  P.status = reinterpret_cast<int *>(jobs[0].h->ws + jobs[0].h->status_off);
+  if ((e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mp.smem)) !=
+      cudaSuccess)
+    return e;
+  const int num_sms = jobs[0].h->num_sms;
+  tc_gemm_kernel<<<mp.units < num_sms ? mp.units : num_sms, kThreads, mp.smem, st>>>(P);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  for (int j = 0; j < nj; ++j) {
+    const JobPlan &p = mp.jp[j];
+    if ((e = psfsim_launch_reduce_partials(reinterpret_cast<float *>(base + p.part_off), p.KS, jobs[j].cap, p.rows,
+                                           jobs[j].h->M, jobs[j].y, jobs[j].count, st)) != cudaSuccess)
+      return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace
 
 size_t psfsim_forward_tc_scratch(const psfsim_plan *h, int B) {
-  const int Bc = B < kMaxBp ? B : kMaxBp;
-  const Chunking c = plan_chunk(h, Bc);
-  return c.xs_bytes + c.part_bytes;
+  JobSpec js{h, nullptr, nullptr, B < kMaxBp ? B : kMaxBp, nullptr};
+  return plan_multi(&js, 1, nullptr).scratch;
 }
 
 cudaError_t psfsim_launch_forward_tc(const psfsim_plan *h, const float *x, int B, float *y, void *scratch,
                                      cudaStream_t st) {
-  const float *scale = reinterpret_cast<const float *>(h->ws + h->scale_off);
-  int *status = reinterpret_cast<int *>(h->ws + h->status_off);
-  const int64_t rows = psfsim_round_up(h->M, BM);
   for (int b0 = 0; b0 < B; b0 += kMaxBp) {
     const int Bc = (B - b0) < kMaxBp ? (B - b0) : kMaxBp;
-    const Chunking c = plan_chunk(h, Bc);
-    __nv_bfloat16 *xs = reinterpret_cast<__nv_bfloat16 *>(scratch);
-    float *part = reinterpret_cast<float *>(static_cast<char *>(scratch) + c.xs_bytes);
-    xsplit_kernel<<<h->num_sms * 8, 256, 0, st>>>(x + (int64_t)b0 * h->K, Bc, c.Bp, h->K, h->ld, scale, xs);
-    cudaError_t e = cudaGetLastError();
+    JobSpec js{h, x + (int64_t)b0 * h->K, y + (int64_t)b0 * h->M, Bc, nullptr};
+    const MultiPlan mp = plan_multi(&js, 1, nullptr);
+    cudaError_t e = launch_multi(&js, 1, mp, scratch, st);
     if (e != cudaSuccess) return e;
-    CUtensorMap mhi, mlo, mx;
-    if (!encode_bf16_2d(&mhi, h->ws + h->a_off, (uint64_t)h->ld, (uint64_t)rows, BK, BM) ||
-        !encode_bf16_2d(&mlo, h->ws + h->lo_off, (uint64_t)h->ld, (uint64_t)rows, BK, BM) ||
-        !encode_bf16_2d(&mx, xs, (uint64_t)h->ld, (uint64_t)(3 * c.Bp), BK, (uint32_t)(3 * c.Bp)))
-      return cudaErrorInvalidValue;
-    TcParams P;
-    P.rows = rows;
-    P.M = h->M;
-    P.B = Bc;
-    P.Bp = c.Bp;
-    P.KS = c.KS;
-    P.m_tiles = c.m_tiles;
-    P.k_tiles = c.k_tiles;
-    P.stages = c.stages;
-    P.chunk = kChunkTiles;
-    P.stage_bytes = c.stage_bytes;
-    P.part = part;
-    P.status = status;
-    if ((e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem)) !=
-        cudaSuccess)
-      return e;
-    const int units = c.m_tiles * c.KS;
-    const int grid = units < h->num_sms ? units : h->num_sms;
-    tc_gemm_kernel<<<grid, kThreads, c.smem, st>>>(mhi, mlo, mx, P);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = psfsim_launch_reduce_partials(part, c.KS, Bc, rows, h->M, y + (int64_t)b0 * h->M, st)) != cudaSuccess)
-      return e;
   }
   return cudaSuccess;
+}
+
+int psfsim_multi_validate(const psfsim_job_t *jobs, int njobs) {
+  if (!jobs || njobs < 1 || njobs > kMaxJobs) return PSFSIM_ERR_ARG;
+  for (int j = 0; j < njobs; ++j) {
+    const psfsim_plan *h = jobs[j].plan;
+    if (!h || !jobs[j].d_x || !jobs[j].d_y || jobs[j].capacity < 1 || jobs[j].capacity > kMaxBp)
+      return PSFSIM_ERR_ARG;
+    if (h->storage != PSFSIM_SPLIT_BF16) return PSFSIM_ERR_UNSUPPORTED;
+    if (h->device != jobs[0].plan->device) return PSFSIM_ERR_ARG;
+  }
+  return PSFSIM_OK;
+}
+
+size_t psfsim_forward_multi_scratch(const psfsim_job_t *jobs, int njobs, const psfsim_tuning_t *tune) {
+  JobSpec js[kMaxJobs];
+  for (int j = 0; j < njobs; ++j) js[j] = JobSpec{jobs[j].plan, jobs[j].d_x, jobs[j].d_y, jobs[j].capacity, jobs[j].d_count};
+  return plan_multi(js, njobs, tune).scratch;
+}
+
+cudaError_t psfsim_launch_forward_multi(const psfsim_job_t *jobs, int njobs, const psfsim_tuning_t *tune,
+                                        void *scratch, cudaStream_t st) {
+  JobSpec js[kMaxJobs];
+  for (int j = 0; j < njobs; ++j) js[j] = JobSpec{jobs[j].plan, jobs[j].d_x, jobs[j].d_y, jobs[j].capacity, jobs[j].d_count};
+  return launch_multi(js, njobs, plan_multi(js, njobs, tune), scratch, st);
 }
