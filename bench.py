@@ -109,6 +109,17 @@ def _workload():
     return w, lib32, x, g
 
 
+def _allreduce_max(value: float, device) -> float:
+    """Max of a per-rank scalar over all ranks (identity on one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _events(n):
     import torch
     return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
@@ -173,10 +184,7 @@ def _gpu_arm(args, rank, world, local_rank):
     elapsed_ms = t0.elapsed_time(t1)
     fwd_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
     adj_ms = float(np.mean([e[2].elapsed_time(e[3]) for e in ev]))
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = _allreduce_max(elapsed_ms, dev)
 
     # e2e: a new observed image arrives from pinned host memory every step and
     # the loss + gradient come back to the host, through the same C-ABI calls
@@ -201,10 +209,7 @@ def _gpu_arm(args, rank, world, local_rank):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = _allreduce_max(e2e_ms, dev)
 
     # plain FP32 GEMV comparator (cuBLAS through torch) on the same stored A
     x = torch.from_numpy(x_np).to(dev)
@@ -282,6 +287,198 @@ def _gpu_arm(args, rank, world, local_rank):
     return out, plan, y_gpu, x_np, w, lib32
 
 
+def _timed(fn, reps, stream):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = _events(2)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _rows_error(lib32, radii, N, S, X, Y, rows, cols=None):
+    """Bound-relative error of Y[:, rows] against the oracle (test-infrastructure leg only)."""
+    from oracle import psfsim_oracle as O
+    xs, ys = O.scene_offsets(N, S)
+    if cols is None:
+        cols = np.arange(N * N)
+    A_r = O.A_rows(lib32.astype(np.float64), radii, xs[cols], ys[cols], rows)
+    X64 = X[:, cols].astype(np.float64)
+    rel = O.bound_relative_error(Y.astype(np.float64), X64 @ A_r.T, np.abs(X64) @ np.abs(A_r).T, floor=O.FLT_MIN)
+    return {"max_bound_rel_error": float(rel.max()), "median": float(np.median(rel)),
+            "rows_checked": int(len(rows)), "scenes_checked": int(X.shape[0])}
+
+
+def _path_batched(dev, stream, hbm, with_oracle):
+    """Batched split-BF16 256^2 workload, one wavelength: 64 scenes through the tcgen05 GEMM."""
+    import torch
+    from paper_2106_09122_gb300 import Plan
+    from synth import workloads
+    w = workloads.batched_256()
+    out = {}
+    lib32 = w.library(0).astype(np.float32)
+    torch.cuda.synchronize()
+    b0, b1 = _events(2)
+    b0.record(stream)
+    plan = Plan(torch.from_numpy(lib32).to(dev), w.radii, w.s, N=w.N, S=w.S, storage="split_bf16")
+    b1.record(stream)
+    torch.cuda.synchronize()
+    X_np = workloads.scene_batch(w, 64).astype(np.float32)
+    X = torch.from_numpy(X_np).to(dev)
+    Y = torch.empty((64, w.M), device=dev)
+    scr = torch.empty(plan.forward_scratch_bytes(64), dtype=torch.uint8, device=dev)
+    ms = _timed(lambda: plan.forward(X, out=Y, scratch=scr), 20, stream)
+    a_bytes = 4 * w.M * w.K + 64 * w.K * 4 + 64 * w.M * 4
+    out.update({"workload": "batched_split_bf16_256: 60 PSFs 256^2 at 0.125 lambda/D, A 65536^2 split-BF16 "
+                            "(17.2 GB), 64 scenes, 1 of 8 wavelengths",
+                "images_per_s": 64 / (ms / 1e3), "ms_per_batch": ms, "build_ms": b0.elapsed_time(b1),
+                "gmac_per_s": 64 * w.M * w.K / (ms / 1e3) / 1e9,
+                "roofline": {"bound": "hbm", "achieved": a_bytes / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                             "frac": a_bytes / (ms / 1e3) / 1e9 / hbm, "kernel": "tc_gemm_kernel (+ split, reduce)"},
+                "status": plan.sync_status()})
+    if with_oracle:
+        rows = np.sort(np.random.default_rng(81).choice(w.M, 24, replace=False))
+        Yr = Y[:8, torch.from_numpy(rows).to(dev)].cpu().numpy()
+        out["error_vs_oracle"] = _rows_error(lib32, w.radii, w.N, w.S, X_np[:8], Yr, rows)
+    del plan, X, Y, scr
+    torch.cuda.empty_cache()
+    return out
+
+
+def _path_fused(dev, stream, with_oracle):
+    """Fused 512^2 workload: A (275 GB in FP32) regenerated on chip for 32 scenes."""
+    import torch
+    from paper_2106_09122_gb300 import Plan
+    from synth import workloads
+    w = workloads.fused_512()
+    lib32 = w.library().astype(np.float32)
+    plan = Plan(torch.from_numpy(lib32).to(dev), w.radii, w.s, N=w.N, S=w.S, storage="fused")
+    X_np = workloads.scene_batch(w, 32, kind="two_ring").astype(np.float32)
+    X = torch.from_numpy(X_np).to(dev)
+    Y = torch.empty((32, w.M), device=dev)
+    scr = torch.empty(plan.forward_scratch_bytes(32), dtype=torch.uint8, device=dev)
+    ms = _timed(lambda: plan.forward(X, out=Y, scratch=scr), 3, stream)
+    props = torch.cuda.get_device_properties(dev)
+    # A elements generated per batch: the x>0, y>0 quadrant of the scene, columns inside the last radius.
+    c = (np.arange(w.N // 2) + 0.5) * w.S
+    q0 = np.hypot(c[:, None], c[None, :]) <= w.radii[-1]
+    elems = int(q0.sum()) * w.M
+    inst_per_elem = 108.0  # ncu: thread instructions per generated element (profiles/fused_kernel_512.md)
+    peak_inst = props.multi_processor_count * 4 * 32 * 2.07e9
+    achieved_inst = elems * inst_per_elem / (ms / 1e3)
+    out = {"workload": "fused_512: 80 PSFs 512^2 at 0.0625 lambda/D, A 262144^2 never stored, 32 two-ring scenes",
+           "images_per_s": 32 / (ms / 1e3), "ms_per_batch": ms,
+           "elements_generated_per_s": elems / (ms / 1e3),
+           "dense_equivalent_gmac_per_s": 32 * w.M * w.K / (ms / 1e3) / 1e9,
+           "roofline": {"bound": "alu", "achieved": achieved_inst / 1e12, "peak": peak_inst / 1e12,
+                        "unit": "Tinst/s", "frac": achieved_inst / peak_inst,
+                        "kernel": "fused_kernel (A-tile generation + tcgen05)",
+                        "peak_source": "SMs x 4 SMSPs x 32 lanes x 2070 MHz issue rate"},
+           "status": plan.sync_status()}
+    if with_oracle:
+        rows = np.sort(np.random.default_rng(82).choice(w.M, 12, replace=False))
+        Yr = Y[:2, torch.from_numpy(rows).to(dev)].cpu().numpy()
+        out["error_vs_oracle"] = _rows_error(lib32, w.radii, w.N, w.S, X_np[:2], Yr, rows)
+    del plan, X, Y, scr
+    torch.cuda.empty_cache()
+    return out
+
+
+def _path_uneven(dev, stream, hbm, with_oracle):
+    """500 scenes of 10 (N, S) buckets, each with its own split-BF16 A; waves of 50 via one CUDA graph."""
+    import torch
+    from paper_2106_09122_gb300 import Plan
+    from paper_2106_09122_gb300.serve import UnevenServer, autotune
+    from synth import workloads
+    w = workloads.adjoint_128()
+    lib32 = w.library().astype(np.float32)
+    lib = torch.from_numpy(lib32).to(dev)
+    buckets = workloads.uneven_buckets()
+    plans = {k: Plan(lib, w.radii, w.s, N=k[0], S=k[1], storage="split_bf16") for k in buckets}
+    rng = np.random.default_rng(w.seed + 9)
+    order = [buckets[i] for i in rng.integers(0, len(buckets), 500)]
+    W = 50
+    waves = [order[i:i + W] for i in range(0, len(order), W)]
+    cap = max(max(wv.count(k) for k in buckets) for wv in waves)
+    server = UnevenServer(plans, capacity=cap)
+    mf = server.mf
+    for j, k in enumerate(server.keys):
+        mf.x[j].copy_(torch.rand(cap, k[0] * k[0], device=dev) * 1e-9)
+    mf.count.fill_(cap)
+    best, best_ms, _ = autotune(mf, chunks=(2, 4, 8), units=(2, 4, 8), reps=3)
+    server.capture()
+    scenes = [workloads.random_ring_scene(k[0], k[1], w.r_max, w.seed + 20000 + i).ravel().astype(np.float32)
+              for i, k in enumerate(order)]
+    server.run_wave([(k, scenes[i]) for i, k in enumerate(waves[0])])  # warm replay
+    lat = []
+    outs = []
+    t0 = time.perf_counter()
+    for wi, wv in enumerate(waves):
+        a = time.perf_counter()
+        outs += server.run_wave([(k, scenes[wi * W + i]) for i, k in enumerate(wv)])
+        lat += [time.perf_counter() - a] * len(wv)
+    total = time.perf_counter() - t0
+    a_bytes = sum(p.M * p.info.ld * 4 for p in plans.values())
+    out = {"workload": "uneven_500: 500 scenes, N in {64,96,128,192,256} x S in {0.3,0.5} lambda/D, per-bucket "
+                       "split-BF16 A (17.3 GB), seeded arrival order, waves of 50 through one CUDA graph",
+           "images_per_s": len(order) / total, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+           "p99_ms": 1e3 * float(np.percentile(lat, 99)), "tuning": {"chunk": best[0], "units_per_sm": best[1]},
+           "multi_launch_ms": best_ms,
+           "roofline": {"bound": "hbm", "achieved": a_bytes / (best_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                        "frac": a_bytes / (best_ms / 1e3) / 1e9 / hbm,
+                        "kernel": "tc_gemm_kernel, 10 jobs in one persistent launch"}}
+    # plain per-scene FP32 GEMV loop (cuBLAS) on FP32 A per bucket
+    fp = {k: Plan(lib, w.radii, w.s, N=k[0], S=k[1]) for k in buckets}
+    xs_dev = [torch.from_numpy(sc).to(dev) for sc in scenes]
+    torch.cuda.synchronize()
+    clat = []
+    c0 = time.perf_counter()
+    for i, k in enumerate(order):
+        a = time.perf_counter()
+        torch.mv(fp[k].A_fp32(), xs_dev[i])
+        torch.cuda.synchronize()
+        clat.append(time.perf_counter() - a)
+    out["fp32_gemv_loop"] = {"images_per_s": len(order) / (time.perf_counter() - c0),
+                             "p50_ms": 1e3 * float(np.percentile(clat, 50)),
+                             "p99_ms": 1e3 * float(np.percentile(clat, 99))}
+    if with_oracle:
+        errs = []
+        pick = np.random.default_rng(83).choice(len(order), 6, replace=False)
+        for i in pick:
+            k = order[i]
+            rows = np.sort(np.random.default_rng(int(i)).choice(w.M, 8, replace=False))
+            e = _rows_error(lib32, w.radii, k[0], k[1], scenes[i][None, :], outs[i].numpy()[rows][None, :], rows)
+            errs.append(e["max_bound_rel_error"])
+        out["error_vs_oracle"] = {"max_bound_rel_error": float(max(errs)), "scenes_checked": len(pick),
+                                  "rows_per_scene": 8}
+    del plans, fp, server, xs_dev, lib
+    torch.cuda.empty_cache()
+    return out
+
+
+def _path_nearest(dev):
+    """Linear vs nearest radial interpolation (Sec. 4.2): % difference of the images within 9 lambda/D."""
+    import torch
+    from paper_2106_09122_gb300 import Plan
+    from synth import workloads
+    w = workloads.adjoint_128()
+    lib = torch.from_numpy(w.library().astype(np.float32)).to(dev)
+    x = torch.from_numpy(workloads.random_ring_scene(w.N, w.S, w.r_max, w.seed + 5).ravel()
+                         .astype(np.float32)).to(dev)
+    yl = Plan(lib, w.radii, w.s, N=w.N, S=w.S).forward(x)
+    yn = Plan(lib, w.radii, w.s, N=w.N, S=w.S, interp="nearest").forward(x)
+    c = (np.arange(w.n) - (w.n - 1) / 2) * w.s
+    inside = torch.from_numpy((np.hypot(c[:, None], c[None, :]) <= 9.0).ravel()).to(dev)
+    pct = (100 * (yl - yn).abs() / yl.abs().clamp_min(1e-30))[inside & (yl.abs() > 0)]
+    return {"workload": "adjoint_fit_128 scene, linear vs nearest radial interpolation",
+            "max_pct_difference_within_9_lambda_over_D": float(pct.max()),
+            "mean_pct_difference_within_9_lambda_over_D": float(pct.mean())}
+
+
 def _oracle_sample(w, lib32, n_cols=512, seed=17):
     """Column sample of the oracle's A (FP64) and the sampled column indices."""
     from oracle import psfsim_oracle as O
@@ -329,7 +526,7 @@ def _cpu_baseline_and_error(w, lib32, x_np, g_np, y_gpu):
     xs, ys = O.scene_offsets(w.N, w.S)
     A_r = O.A_rows(lib32.astype(np.float64), w.radii, xs, ys, rows)
     x64 = x_np.astype(np.float64)
-    rel = O.bound_relative_error(y_gpu[rows], A_r @ x64, np.abs(A_r) @ np.abs(x64))
+    rel = O.bound_relative_error(y_gpu[rows], A_r @ x64, np.abs(A_r) @ np.abs(x64), floor=O.FLT_MIN)
     err = {"max_bound_rel_error": float(rel.max()), "median": float(np.median(rel)),
            "rows_checked": int(len(rows)), "tolerance": 1e-5}
     return base, err
@@ -366,6 +563,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="psfsim", choices=["psfsim", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--main-only", action="store_true", help="skip the other workloads' measurements")
     args = ap.parse_args()
     rank, world, local_rank = _dist()
     if args.impl == "reference":
@@ -381,6 +579,19 @@ def main():
         _, _, _, g_np = _workload()
         out["cpu_baseline"], out["error_vs_oracle"] = _cpu_baseline_and_error(
             w, lib32, x_np, g_np, y.double().cpu().numpy())
+    if not args.main_only and world == 1:
+        del plan, y
+        torch.cuda.empty_cache()
+        dev = torch.device("cuda", local_rank)
+        stream = torch.cuda.current_stream()
+        hbm, _, _ = _peaks()
+        oracle_ok = rank == 0 and world == 1 and not args.no_cpu_baseline
+        out["other_workloads"] = {
+            "batched_split_bf16_256": _path_batched(dev, stream, hbm, oracle_ok),
+            "fused_512": _path_fused(dev, stream, oracle_ok),
+            "uneven_500": _path_uneven(dev, stream, hbm, oracle_ok),
+            "nearest_vs_linear_128": _path_nearest(dev),
+        }
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

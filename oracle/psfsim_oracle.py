@@ -176,11 +176,19 @@ def error_bound(A: np.ndarray, x: np.ndarray) -> np.ndarray:
     return forward(np.abs(A), np.abs(x))
 
 
-def bound_relative_error(y, y_ref, bound) -> np.ndarray:
-    """|y - y_ref| / bound, with 0/0 = 0 and e/0 = inf."""
+FLT_MIN = float(np.finfo(np.float32).tiny)
+
+
+def bound_relative_error(y, y_ref, bound, floor: float = 0.0) -> np.ndarray:
+    """|y - y_ref| / max(bound, floor), with 0/0 = 0 and e/0 = inf.
+
+    A float32 result below FLT_MIN is subnormal and carries only absolute
+    precision, so comparisons of float32 images pass floor=FLT_MIN: pixels
+    whose bound lies below the normal range are then held to 1e-5 * FLT_MIN.
+    """
     y = np.asarray(y, dtype=np.float64)
     err = np.abs(y - np.asarray(y_ref, dtype=np.float64))
-    bound = np.asarray(bound, dtype=np.float64)
+    bound = np.maximum(np.asarray(bound, dtype=np.float64), floor)
     with np.errstate(divide="ignore", invalid="ignore"):
         rel = np.where(bound > 0.0, err / np.where(bound > 0.0, bound, 1.0),
                        np.where(err > 0.0, np.inf, 0.0))

@@ -34,7 +34,7 @@ def test_fused_forward_matches_oracle(n, N, S, B):
     assert plan.sync_status() == 0
     for b in range(B):
         x64 = x[b].astype(np.float64)
-        rel = O.bound_relative_error(y[b], O.forward(A, x64), O.error_bound(A, x64))
+        rel = O.bound_relative_error(y[b], O.forward(A, x64), O.error_bound(A, x64), floor=O.FLT_MIN)
         assert rel.max() <= TOL, (b, rel.max())
 
 
@@ -60,7 +60,7 @@ def test_fused_512_crop_against_oracle_and_stored_path():
     A_r = O.A_rows(lib32.astype(np.float64), w.radii, xs[cols], ys[cols], rows)
     Xc = X[:, cols].astype(np.float64)
     Yr = Y[:, torch.from_numpy(rows).to(DEV)].double().cpu().numpy()
-    rel = O.bound_relative_error(Yr, Xc @ A_r.T, np.abs(Xc) @ np.abs(A_r).T)
+    rel = O.bound_relative_error(Yr, Xc @ A_r.T, np.abs(Xc) @ np.abs(A_r).T, floor=O.FLT_MIN)
     assert rel.max() <= TOL, rel.max()
     # stored split-BF16 path over the crop's field points
     pts = np.stack([xs[cols], ys[cols]], axis=1)

@@ -64,7 +64,7 @@ def test_tensor_core_forward_small(B):
     assert plan.sync_status() == 0
     for b in range(B):
         x64 = x[b].astype(np.float64)
-        rel = O.bound_relative_error(y[b], O.forward(A, x64), O.error_bound(A, x64))
+        rel = O.bound_relative_error(y[b], O.forward(A, x64), O.error_bound(A, x64), floor=O.FLT_MIN)
         assert rel.max() <= 1e-5, (b, rel.max())
 
 
@@ -97,5 +97,5 @@ def test_batched_256_workload_sampled_rows():
     A_r = O.A_rows(lib32.astype(np.float64), w.radii, xs, ys, rows)
     X64 = X.astype(np.float64)
     Yr = Y[:, torch.from_numpy(rows).to(DEV)].double().cpu().numpy()
-    rel = O.bound_relative_error(Yr, X64 @ A_r.T, np.abs(X64) @ np.abs(A_r).T)
+    rel = O.bound_relative_error(Yr, X64 @ A_r.T, np.abs(X64) @ np.abs(A_r).T, floor=O.FLT_MIN)
     assert rel.max() <= 1e-5, rel.max()

@@ -26,7 +26,7 @@ def _setup(seed=71):
 
 def _check(y, A, x):
     x64 = np.asarray(x, dtype=np.float64)
-    rel = O.bound_relative_error(np.asarray(y, dtype=np.float64), A @ x64, np.abs(A) @ np.abs(x64))
+    rel = O.bound_relative_error(np.asarray(y, dtype=np.float64), A @ x64, np.abs(A) @ np.abs(x64), floor=O.FLT_MIN)
     assert rel.max() <= 1e-5, rel.max()
 
 
