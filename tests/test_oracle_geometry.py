@@ -192,8 +192,8 @@ def test_against_scipy_routines_named_by_the_paper():
 
 def test_error_metric_floor_below_float32_normal_range():
     """Float32 results below FLT_MIN are subnormal: compared at 1e-5 * FLT_MIN absolute."""
-    rel = O.bound_relative_error([2.0e-40, 1.0], [2.1e-40, 1.0 + 1e-6], [2.1e-40, 1.0], floor=O.FLT_MIN)
-    assert rel[0] == pytest.approx(1e-41 / O.FLT_MIN) and rel[0] < 1e-5
+    rel = O.bound_relative_error([2.0e-40, 1.0], [2.0001e-40, 1.0 + 1e-6], [2.0e-40, 1.0], floor=O.FLT_MIN)
+    assert rel[0] == pytest.approx(1e-44 / O.FLT_MIN) and rel[0] < 1e-5
     assert rel[1] == pytest.approx(1e-6)
     assert O.bound_relative_error([1.0], [1.0], [0.0])[0] == 0.0
     assert np.isinf(O.bound_relative_error([1.0], [0.0], [0.0])[0])
