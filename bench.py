@@ -32,6 +32,17 @@ sys.path.insert(0, ROOT)
 METRIC = "simulated images/s and GMAC/s (fraction of HBM/tensor roofline) vs plain FP32 GEMV at stated error"
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of the current kernels (profiles/*.md).  The tensor-core figure is
+# from the 128^2 case and scales with the bytes of A (traffic / A = 1.0375 there).
+NCU_TRAFFIC = {
+    "forward": 1.073844e9 + 0.003246e9,        # fwd_partial_kernel, 128^2
+    "adjoint": 1.073871e9 + 0.002845e9,        # adj_kernel, 128^2
+    "tc_gemm_per_A_byte": (1.086450e9 + 0.028076e9) / (16384 * 16384 * 4),
+    "fused": 185.607936e6 + 111.038720e6,      # fused_kernel, 512^2, 32 scenes
+}
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -267,7 +278,7 @@ def _gpu_arm(args, rank, world, local_rank):
         "gmac_per_s": images * 2 * w.M * w.K / (elapsed_ms / 1e3) / 1e9,
         "kernels_ms": {"forward": fwd_ms, "adjoint": adj_ms, "build_once": build_ms},
         "roofline": {"bound": "hbm", "achieved": dom_bytes / (dom_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-                     "frac": dom_bytes / (dom_ms / 1e3) / 1e9 / hbm, "traffic": None,
+                     "frac": dom_bytes / (dom_ms / 1e3) / 1e9 / hbm, "traffic": NCU_TRAFFIC[dominant] / 1e9,
                      "kernel": f"psfsim {dominant} (A streamed once per launch)",
                      "peak_source": f"{peak_kind} hbm_gbs"},
         "roofline_frac": {"forward": fwd_bytes / (fwd_ms / 1e3) / 1e9 / hbm,
@@ -338,7 +349,9 @@ def _path_batched(dev, stream, hbm, with_oracle):
                 "images_per_s": 64 / (ms / 1e3), "ms_per_batch": ms, "build_ms": b0.elapsed_time(b1),
                 "gmac_per_s": 64 * w.M * w.K / (ms / 1e3) / 1e9,
                 "roofline": {"bound": "hbm", "achieved": a_bytes / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-                             "frac": a_bytes / (ms / 1e3) / 1e9 / hbm, "kernel": "tc_gemm_kernel (+ split, reduce)"},
+                             "frac": a_bytes / (ms / 1e3) / 1e9 / hbm, "kernel": "tc_gemm_kernel (+ split, reduce)",
+                             "traffic": NCU_TRAFFIC["tc_gemm_per_A_byte"] * 4 * w.M * w.K / 1e9,
+                             "traffic_note": "ncu on the 128^2 case, scaled by the bytes of A"},
                 "status": plan.sync_status()})
     if with_oracle:
         rows = np.sort(np.random.default_rng(81).choice(w.M, 24, replace=False))
@@ -377,6 +390,7 @@ def _path_fused(dev, stream, with_oracle):
            "roofline": {"bound": "alu", "achieved": achieved_inst / 1e12, "peak": peak_inst / 1e12,
                         "unit": "Tinst/s", "frac": achieved_inst / peak_inst,
                         "kernel": "fused_kernel (A-tile generation + tcgen05)",
+                        "traffic": NCU_TRAFFIC["fused"] / 1e9, "traffic_unit": "GB",
                         "peak_source": "SMs x 4 SMSPs x 32 lanes x 2070 MHz issue rate"},
            "status": plan.sync_status()}
     if with_oracle:
@@ -556,6 +570,43 @@ def _reference_arm(args):
             "e2e": {"value": value, "unit": "images/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def _profile_case(name: str) -> None:
+    """A few launches of one workload, small enough for a full ncu capture."""
+    import torch
+    from paper_2106_09122_gb300 import Plan
+    from synth import workloads
+    dev = "cuda:0"
+    if name == "fused512":
+        w = workloads.fused_512()
+        plan = Plan(torch.from_numpy(w.library().astype(np.float32)).to(dev), w.radii, w.s, N=w.N, S=w.S,
+                    storage="fused")
+        X = torch.from_numpy(workloads.scene_batch(w, 32, kind="two_ring").astype(np.float32)).to(dev)
+        for _ in range(2):
+            plan.forward(X)
+    elif name == "tc128":
+        w = workloads.adjoint_128()
+        plan = Plan(torch.from_numpy(w.library().astype(np.float32)).to(dev), w.radii, w.s, N=w.N, S=w.S,
+                    storage="split_bf16")
+        X = torch.rand(64, w.K, device=dev)
+        for _ in range(3):
+            plan.forward(X)
+        g = torch.rand(1, w.M, device=dev)
+        for _ in range(3):
+            plan.adjoint(g)
+    elif name == "fp32_128":
+        w = workloads.adjoint_128()
+        plan = Plan(torch.from_numpy(w.library().astype(np.float32)).to(dev), w.radii, w.s, N=w.N, S=w.S)
+        x = torch.rand(w.K, device=dev)
+        g = torch.rand(w.M, device=dev)
+        for _ in range(3):
+            plan.forward(x)
+            plan.adjoint(g)
+    else:
+        raise SystemExit(f"unknown case {name}")
+    torch.cuda.synchronize()
+    print(json.dumps({"case": name, "status": plan.sync_status()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -564,7 +615,11 @@ def main():
     ap.add_argument("--impl", default="psfsim", choices=["psfsim", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--main-only", action="store_true", help="skip the other workloads' measurements")
+    ap.add_argument("--case", default=None, help="run one small profiling case (fp32_128, tc128, fused512)")
     args = ap.parse_args()
+    if args.case:
+        _profile_case(args.case)
+        return
     rank, world, local_rank = _dist()
     if args.impl == "reference":
         out = _reference_arm(args)

@@ -240,8 +240,9 @@ __global__ void __launch_bounds__(512) build_fp32_kernel(const __grid_constant__
   for (int64_t pos = begin; pos < end;) {
     const int j0 = P.order[pos];
     const int k = P.geom[j0].k;
-    const int bucket = column_bucket(P.geom[j0], P.n_r);
-    const int64_t gend = min(end, (int64_t)P.bstart[bucket + 1]);
+    // All columns of one radial bracket (every angle bin) share the staged pair.
+    const int group_end = k < 0 ? psfsim_num_buckets(P.n_r) : (k + 1) * PSFSIM_THETA_BINS;
+    const int64_t gend = min(end, (int64_t)P.bstart[group_end]);
     if (kSmem && k >= 0 && k != cur_k) {
       __syncthreads();  // every warp is done with the previous pair
       if (threadIdx.x == 0) {
