@@ -84,8 +84,8 @@ int psfsim_workspace_bytes(int n, int n_r, int64_t K, int storage, size_t *bytes
 /* Build the interpolated PSF library A for a scene grid (Sec. 2, the loop over
  * all N^2 scene pixels; Eq. 4-5).
  *   d_lib       device float32 [n_r][n][n], 16-byte aligned; read during the
- *               build only (FUSED storage keeps its own zero-bordered copy in
- *               the workspace).  FUSED needs an even N (it uses the exact
+ *               build only (FUSED storage keeps its own copy in the
+ *               workspace, each pixel's 2 x 2 bilinear footprint as a float4).  FUSED needs an even N (it uses the exact
  *               quarter-turn symmetry of the scene grid) and synchronizes the
  *               stream once.
  *   h_radii     host double [n_r], strictly increasing offsets in lambda/D.

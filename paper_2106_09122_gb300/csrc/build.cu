@@ -294,8 +294,8 @@ WsLayout psfsim_layout(int n, int64_t K, int storage, int n_r) {
   L.pts_off = take(K * 16);
   L.status_off = take(16);
   L.libmax_off = take(PSFSIM_MAX_RADII * 4);
-  // FUSED keeps a copy of the library with a one-pixel zero border.
-  L.plib_off = storage == PSFSIM_FUSED ? take((int64_t)n_r * (n + 2) * (n + 2) * 4) : -1;
+  // FUSED keeps a copy of the library in quad layout (2 x 2 footprints as float4).
+  L.plib_off = storage == PSFSIM_FUSED ? take((int64_t)n_r * (n + 1) * (n + 1) * 16) : -1;
   L.total = off;
   (void)n_r;
   return L;
@@ -351,7 +351,7 @@ cudaError_t psfsim_launch_build(psfsim_plan *h, cudaStream_t st) {
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
       return e;
     h->K_valid = kv;
-    return psfsim_launch_pad_library(h, st);
+    return psfsim_launch_quad_library(h, st);
   }
   if (h->storage == PSFSIM_SPLIT_BF16) return psfsim_launch_split_build(h, st);
   if (h->storage != PSFSIM_FP32) return cudaErrorNotSupported;

@@ -47,11 +47,11 @@ constexpr int kBlockQ = 16, kBlockP = 8;
 
 struct FusedParams {
   int n, N, Bp, B, KS, m_tiles, k_tiles, stages, tiles_q;
-  int64_t M, rows, K0v, psz;  // psz: floats per zero-padded PSF, (n + 2)^2
+  int64_t M, rows, K0v, psz;  // psz: float4 entries per quad-layout PSF, (n + 1)^2
   uint32_t stage_bytes;
   const ColGeom *geom;
   const int *order;
-  const float *plib;  // library with a one-pixel zero border, [n_r][n+2][n+2]
+  const float4 *qlib; // quad-layout library, [n_r][(n+1)^2]
   float *part;        // [KS][4][B][M]
   int *status;
 };
@@ -64,14 +64,21 @@ struct ColEntry {
   float w0, w1;
 };
 
-__global__ void pad_library_kernel(const float *__restrict__ lib, int n, int n_r, float *__restrict__ plib) {
-  const int np = n + 2;
-  const int64_t total = (int64_t)n_r * np * np;
+// Library in "quad" layout: for every padded pixel (p, q), p, q in [-1, n-1],
+// the float4 (L[p][q], L[p][q+1], L[p+1][q], L[p+1][q+1]) with zeros outside
+// the PSF, so the whole bilinear footprint of a sample is one aligned 16-byte
+// load.  Indexed [k][(p+1)(n+1) + (q+1)].
+__global__ void quad_library_kernel(const float *__restrict__ lib, int n, int n_r, float4 *__restrict__ qlib) {
+  const int nq = n + 1;
+  const int64_t total = (int64_t)n_r * nq * nq;
+  auto at = [&](int64_t k, int p, int q) -> float {
+    return (p >= 0 && p < n && q >= 0 && q < n) ? lib[(k * n + p) * n + q] : 0.f;
+  };
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k = t / ((int64_t)np * np);
-    const int rem = (int)(t % ((int64_t)np * np));
-    const int p = rem / np - 1, q = rem % np - 1;
-    plib[t] = (p >= 0 && p < n && q >= 0 && q < n) ? lib[(k * n + p) * n + q] : 0.f;
+    const int64_t k = t / ((int64_t)nq * nq);
+    const int rem = (int)(t % ((int64_t)nq * nq));
+    const int p = rem / nq - 1, q = rem % nq - 1;
+    qlib[t] = make_float4(at(k, p, q), at(k, p, q + 1), at(k, p + 1, q), at(k, p + 1, q + 1));
   }
 }
 
@@ -103,10 +110,10 @@ __global__ void fused_xgather(const float *__restrict__ x, int B, int Bp, int N,
 }
 
 // One A element from a column-table entry; (du2, dv2) = twice the pixel's
-// offset from the tile origin.  Taps come from the zero-padded library, so
-// only the whole 2 x 2 footprint needs a range check.
-__device__ __forceinline__ float gen_element(const ColEntry &e, const float *__restrict__ plib, int n, int np,
-                                             int64_t psz, int du2, int dv2) {
+// offset from the tile origin.  The 2 x 2 footprint of each PSF is one float4
+// of the quad-layout library, so only the footprint position needs a check.
+__device__ __forceinline__ float gen_element(const ColEntry &e, const float4 *__restrict__ qlib, int n,
+                                             int64_t qsz, int du2, int dv2) {
   constexpr int kShift = PSFSIM_FRAC_BITS + 1;
   const long long a2 = e.A0 + e.C * du2 + e.S * dv2;
   const long long b2 = e.B0 - e.S * du2 + e.C * dv2;
@@ -120,12 +127,13 @@ __device__ __forceinline__ float gen_element(const ColEntry &e, const float *__r
   const float wa0 = fa ? __uint2float_rn(0u - fa) * kInv32 : 1.f;
   const float wb1 = __uint2float_rn(fb) * kInv32;
   const float wb0 = fb ? __uint2float_rn(0u - fb) * kInv32 : 1.f;
-  const float *L0 = plib + e.off + (int64_t)(p0 + 1) * np + (q0 + 1);
-  const float v0 = wb0 * (wa0 * __ldg(L0) + wa1 * __ldg(L0 + 1)) + wb1 * (wa0 * __ldg(L0 + np) + wa1 * __ldg(L0 + np + 1));
+  const float4 *Q0 = qlib + e.off + (int64_t)(p0 + 1) * (n + 1) + (q0 + 1);
+  const float4 t0 = __ldg(Q0);
+  const float v0 = wb0 * (wa0 * t0.x + wa1 * t0.y) + wb1 * (wa0 * t0.z + wa1 * t0.w);
   float v1 = 0.f;
   if (e.w1 != 0.f) {
-    const float *L1 = L0 + psz;
-    v1 = wb0 * (wa0 * __ldg(L1) + wa1 * __ldg(L1 + 1)) + wb1 * (wa0 * __ldg(L1 + np) + wa1 * __ldg(L1 + np + 1));
+    const float4 t1 = __ldg(Q0 + qsz);
+    v1 = wb0 * (wa0 * t1.x + wa1 * t1.y) + wb1 * (wa0 * t1.z + wa1 * t1.w);
   }
   return e.w0 * v0 + e.w1 * v1;
 }
@@ -274,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int rot = g >> 2;              // rotation whose accumulator columns this warp drains
     const int cgrp = g >> 2;             // 16-column group this warp generates
     const int r = quarter * 32 + lane;   // tile row
-    const int n = P.n, np = n + 2;
+    const int n = P.n;
     const long long h = n - 1;
     const long long base = h << PSFSIM_FRAC_BITS;
     const int du2 = 2 * (r % kBlockQ), dv2 = 2 * (r / kBlockQ);
@@ -352,8 +360,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int cc = 0; cc < 16; cc += 2) {
             float v0 = 0.f, v1 = 0.f;
             if (row_ok) {
-              v0 = gen_element(tab[cgrp * 16 + cc], P.plib, n, np, P.psz, du2, dv2);
-              v1 = gen_element(tab[cgrp * 16 + cc + 1], P.plib, n, np, P.psz, du2, dv2);
+              v0 = gen_element(tab[cgrp * 16 + cc], P.qlib, n, P.psz, du2, dv2);
+              v1 = gen_element(tab[cgrp * 16 + cc + 1], P.qlib, n, P.psz, du2, dv2);
             }
             const uint32_t hp = pack_bf16(v0, v1);
             hw[cc >> 1] = hp;
@@ -449,9 +457,9 @@ FusedPlanInfo fused_info(const psfsim_plan *h, int Bc) {
 
 }  // namespace
 
-cudaError_t psfsim_launch_pad_library(psfsim_plan *h, cudaStream_t st) {
-  pad_library_kernel<<<h->num_sms * 4, 256, 0, st>>>(h->d_lib, h->n, h->n_r,
-                                                     reinterpret_cast<float *>(h->ws + h->plib_off));
+cudaError_t psfsim_launch_quad_library(psfsim_plan *h, cudaStream_t st) {
+  quad_library_kernel<<<h->num_sms * 4, 256, 0, st>>>(h->d_lib, h->n, h->n_r,
+                                                      reinterpret_cast<float4 *>(h->ws + h->plib_off));
   return cudaGetLastError();
 }
 
@@ -485,7 +493,7 @@ cudaError_t psfsim_launch_forward_fused(const psfsim_plan *h, const float *x, in
     P.KS = f.KS;
     P.m_tiles = f.m_tiles;
     P.tiles_q = f.tiles_q;
-    P.psz = (int64_t)(h->n + 2) * (h->n + 2);
+    P.psz = (int64_t)(h->n + 1) * (h->n + 1);
     P.k_tiles = f.k_tiles;
     P.stages = f.stages;
     P.M = h->M;
@@ -494,7 +502,7 @@ cudaError_t psfsim_launch_forward_fused(const psfsim_plan *h, const float *x, in
     P.stage_bytes = f.stage_bytes;
     P.geom = reinterpret_cast<const ColGeom *>(h->ws + h->geom_off);
     P.order = order;
-    P.plib = reinterpret_cast<const float *>(h->ws + h->plib_off);
+    P.qlib = reinterpret_cast<const float4 *>(h->ws + h->plib_off);
     P.part = part;
     P.status = status;
     if ((e = cudaFuncSetAttribute(fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem)) !=

@@ -51,7 +51,7 @@ def test_workspace_bytes_covers_A(lib):
     assert lib.psfsim_workspace_bytes(128, 40, 128 * 128, B.SPLIT_BF16, ctypes.byref(out)) == B.OK
     assert out.value >= 2 * 2 * 128 * 128 * 128 * 128
     assert lib.psfsim_workspace_bytes(512, 80, 512 * 512, B.FUSED, ctypes.byref(out)) == B.OK
-    assert 80 * 514 * 514 * 4 <= out.value < 200 * 2 ** 20
+    assert 80 * 513 * 513 * 16 <= out.value < 500 * 2 ** 20
     assert lib.psfsim_workspace_bytes(0, 4, 10, B.FP32, ctypes.byref(out)) == B.ERR_ARG
     assert lib.psfsim_workspace_bytes(16, 1, 10, B.FP32, ctypes.byref(out)) == B.ERR_ARG
     assert lib.psfsim_workspace_bytes(16, 4, 10, 7, ctypes.byref(out)) == B.ERR_ARG
