@@ -54,10 +54,13 @@ enum psfsim_status {
 /* Storage of A.  FP32: column-major float32 (each PSF contiguous, as the
  * paper saves one flattened PSF per iteration, Sec. 2).  SPLIT_BF16: row-major
  * bf16 hi + lo with a power-of-two float32 scale per column, for the
- * tensor-core path.  FUSED: A is never stored; tiles are regenerated from the
- * library on every product (the paper's "standard interpolation method",
- * Table 4, done on chip). */
-enum psfsim_storage { PSFSIM_FP32 = 0, PSFSIM_SPLIT_BF16 = 1, PSFSIM_FUSED = 3 };
+ * tensor-core path.  FP32_SYM: FP32 columns of the x > 0, y > 0 quadrant only,
+ * inside the last radius: the other three quadrants' columns are exact
+ * quarter turns of these and the rest are zero (even N, grid builds only;
+ * same results as FP32 up to the order of the sums).  FUSED: A is never
+ * stored; tiles are regenerated from the library on every product (the
+ * paper's "standard interpolation method", Table 4, done on chip). */
+enum psfsim_storage { PSFSIM_FP32 = 0, PSFSIM_SPLIT_BF16 = 1, PSFSIM_FP32_SYM = 2, PSFSIM_FUSED = 3 };
 
 /* Radial interpolation (Sec. 2 compares linear and nearest). */
 enum psfsim_interp { PSFSIM_LINEAR = 0, PSFSIM_NEAREST = 1 };
@@ -71,6 +74,7 @@ typedef struct {
   int64_t lo_offset;    /* SPLIT_BF16: lo (else -1) */
   int64_t scale_offset; /* SPLIT_BF16: float32 per-column scale (else -1) */
   int64_t workspace_bytes;
+  int64_t K_stored;     /* columns held (K; FP32_SYM / FUSED: quadrant columns inside the last radius) */
 } psfsim_info_t;
 
 /* Human-readable name of a status code (static string). */

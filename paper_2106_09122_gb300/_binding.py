@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpsfsim.so")
 
 OK, ERR_ARG, ERR_RADII, ERR_WORKSPACE, ERR_CUDA, ERR_UNSUPPORTED, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
-FP32, SPLIT_BF16, FUSED = 0, 1, 3
+FP32, SPLIT_BF16, FP32_SYM, FUSED = 0, 1, 2, 3
 LINEAR, NEAREST = 0, 1
 STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
 
@@ -24,7 +24,7 @@ i32, i64, f64 = ctypes.c_int, ctypes.c_int64, ctypes.c_double
 class Info(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int32), ("interp", ctypes.c_int32), ("n", ctypes.c_int32),
                 ("n_r", ctypes.c_int32), ("M", i64), ("K", i64), ("ld", i64), ("a_offset", i64),
-                ("lo_offset", i64), ("scale_offset", i64), ("workspace_bytes", i64)]
+                ("lo_offset", i64), ("scale_offset", i64), ("workspace_bytes", i64), ("K_stored", i64)]
 
 
 class Job(ctypes.Structure):

@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(1024) bracket_sort_kernel(const ColGeom *geom,
 }
 
 struct BuildParams {
-  int n, n_r, Wp, pad;
+  int n, n_r, Wp, compact;  // compact: column c of the sorted list is stored at position c
   int64_t K, ld;
   const ColGeom *geom;
   const int *order;
@@ -159,10 +159,10 @@ __device__ __forceinline__ float rotated_value(long long a2, long long b2, int n
 
 // Writes column j of A (FP32, column-major) with one warp.
 template <bool kSmem, bool kVec4>
-__device__ __forceinline__ void build_column(const BuildParams &P, int j, const float *s0,
+__device__ __forceinline__ void build_column(const BuildParams &P, int j, int64_t dest, const float *s0,
                                              const float *s1, int lane) {
   const ColGeom g = P.geom[j];
-  float *col = P.A + (int64_t)j * P.ld;
+  float *col = P.A + dest * P.ld;
   const int n = P.n;
   const int64_t M = (int64_t)n * n;
   if (g.k < 0) {
@@ -257,8 +257,10 @@ __global__ void __launch_bounds__(512) build_fp32_kernel(const __grid_constant__
         return;
       }
     }
-    for (int64_t c = pos + warp; c < gend; c += nwarps)
-      build_column<kSmem, kVec4>(P, P.order[c], s0, s1, lane);
+    for (int64_t c = pos + warp; c < gend; c += nwarps) {
+      const int j = P.order[c];
+      build_column<kSmem, kVec4>(P, j, P.compact ? c : (int64_t)j, s0, s1, lane);
+    }
     pos = gend;
   }
 }
@@ -275,9 +277,10 @@ WsLayout psfsim_layout(int n, int64_t K, int storage, int n_r) {
     return at;
   };
   L.lo_off = L.scale_off = -1;
-  if (storage == PSFSIM_FP32) {
+  if (storage == PSFSIM_FP32 || storage == PSFSIM_FP32_SYM) {
     L.ld = psfsim_round_up(M, 32);
-    L.a_off = take(L.ld * K * 4);
+    // FP32_SYM stores at most the x > 0, y > 0 quadrant's columns.
+    L.a_off = take(L.ld * (storage == PSFSIM_FP32_SYM ? (K + 3) / 4 : K) * 4);
   } else if (storage == PSFSIM_SPLIT_BF16) {
     L.ld = psfsim_round_up(K, 64);
     const int64_t rows = psfsim_round_up(M, 128);
@@ -343,7 +346,7 @@ cudaError_t psfsim_launch_build(psfsim_plan *h, cudaStream_t st) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   bracket_sort_kernel<<<1, 1024, 0, st>>>(geom, h->Kg, h->n_r, order, bstart);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (h->storage == PSFSIM_FUSED) {
+  if (h->quadrant) {
     // The host needs the number of columns inside the last radius to size launches.
     int kv = 0;
     if ((e = cudaMemcpyAsync(&kv, bstart + psfsim_num_buckets(h->n_r) - 1, sizeof(int), cudaMemcpyDeviceToHost,
@@ -351,10 +354,11 @@ cudaError_t psfsim_launch_build(psfsim_plan *h, cudaStream_t st) {
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
       return e;
     h->K_valid = kv;
-    return psfsim_launch_quad_library(h, st);
+    if (h->storage == PSFSIM_FUSED) return psfsim_launch_quad_library(h, st);
   }
   if (h->storage == PSFSIM_SPLIT_BF16) return psfsim_launch_split_build(h, st);
-  if (h->storage != PSFSIM_FP32) return cudaErrorNotSupported;
+  if (h->storage != PSFSIM_FP32 && h->storage != PSFSIM_FP32_SYM) return cudaErrorNotSupported;
+  const bool compact = h->storage == PSFSIM_FP32_SYM;
 
   const int n = h->n;
   const int Wp = (int)psfsim_round_up(n, 4) + 8;
@@ -366,8 +370,8 @@ cudaError_t psfsim_launch_build(psfsim_plan *h, cudaStream_t st) {
   P.n = n;
   P.n_r = h->n_r;
   P.Wp = Wp;
-  P.pad = 0;
-  P.K = h->K;
+  P.compact = compact ? 1 : 0;
+  P.K = compact ? h->K_valid : h->K;
   P.ld = h->ld;
   P.geom = geom;
   P.order = order;

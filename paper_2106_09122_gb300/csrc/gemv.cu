@@ -214,6 +214,57 @@ cudaError_t adj_group(const psfsim_plan *h, const float *g, int b0, float *gx, b
 
 }  // namespace
 
+cudaError_t psfsim_launch_gemv_partials(const float *A, int64_t ld, int64_t K, const float *x, int B, float *part,
+                                        int KS, cudaStream_t st) {
+  dim3 grid((unsigned)((ld + kRowsPerCta - 1) / kRowsPerCta), (unsigned)KS);
+  int b0 = 0;
+  while (b0 < B) {
+    const int left = B - b0;
+    if (left >= 8) { fwd_partial_kernel<8><<<grid, kFwdThreads, 0, st>>>(A, ld, K, x, B, b0, part); b0 += 8; }
+    else if (left >= 4) { fwd_partial_kernel<4><<<grid, kFwdThreads, 0, st>>>(A, ld, K, x, B, b0, part); b0 += 4; }
+    else if (left >= 2) { fwd_partial_kernel<2><<<grid, kFwdThreads, 0, st>>>(A, ld, K, x, B, b0, part); b0 += 2; }
+    else { fwd_partial_kernel<1><<<grid, kFwdThreads, 0, st>>>(A, ld, K, x, B, b0, part); b0 += 1; }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+int psfsim_gemv_splits(int64_t ld, int64_t K, int num_sms) {
+  const int64_t row_blocks = (ld + kRowsPerCta - 1) / kRowsPerCta;
+  int64_t ks = (int64_t)num_sms * 8 / row_blocks;
+  ks = ks < 1 ? 1 : ks;
+  const int64_t max_ks = K / 8 > 0 ? K / 8 : 1;
+  return (int)(ks < max_ks ? ks : max_ks);
+}
+
+cudaError_t psfsim_launch_adjoint_cols(const float *A, int64_t ld, int64_t M, int64_t K, const float *g, int B,
+                                       float *gx, int num_sms, cudaStream_t st) {
+  const bool vec = (M % 4 == 0) && ((reinterpret_cast<uintptr_t>(g) & 15) == 0);
+  int b0 = 0;
+  while (b0 < B) {
+    const int left = B - b0;
+    const int bb = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+    auto launch = [&](auto kern) -> cudaError_t {
+      int per_sm = 1;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kAdjThreads, 0);
+      if (e != cudaSuccess) return e;
+      int64_t grid = (int64_t)num_sms * (per_sm < 1 ? 1 : per_sm);
+      if (grid > K) grid = K;
+      kern<<<(unsigned)grid, kAdjThreads, 0, st>>>(A, ld, M, K, g, b0, gx);
+      return cudaGetLastError();
+    };
+    cudaError_t e;
+    if (bb == 8) e = vec ? launch(adj_kernel<8, true>) : launch(adj_kernel<8, false>);
+    else if (bb == 4) e = vec ? launch(adj_kernel<4, true>) : launch(adj_kernel<4, false>);
+    else if (bb == 2) e = vec ? launch(adj_kernel<2, true>) : launch(adj_kernel<2, false>);
+    else e = vec ? launch(adj_kernel<1, true>) : launch(adj_kernel<1, false>);
+    if (e != cudaSuccess) return e;
+    b0 += bb;
+  }
+  return cudaSuccess;
+}
+
 size_t psfsim_forward_fp32_scratch(const psfsim_plan *h, int B) {
   return (size_t)forward_splits(h) * (size_t)B * (size_t)h->ld * 4;
 }

@@ -73,6 +73,19 @@ int psfsim_multi_validate(const psfsim_job_t *jobs, int njobs);
 size_t psfsim_forward_multi_scratch(const psfsim_job_t *jobs, int njobs, const psfsim_tuning_t *tune);
 cudaError_t psfsim_launch_forward_multi(const psfsim_job_t *jobs, int njobs, const psfsim_tuning_t *tune,
                                         void *scratch, cudaStream_t st);
+// Generic FP32 GEMV pieces (column-major A) used by several storages.
+int psfsim_gemv_splits(int64_t ld, int64_t K, int num_sms);
+cudaError_t psfsim_launch_gemv_partials(const float *A, int64_t ld, int64_t K, const float *x, int B, float *part,
+                                        int KS, cudaStream_t st);
+cudaError_t psfsim_launch_adjoint_cols(const float *A, int64_t ld, int64_t M, int64_t K, const float *g, int B,
+                                       float *gx, int num_sms, cudaStream_t st);
+// FP32 storage compacted by the quarter-turn symmetry and zero columns.
+size_t psfsim_forward_sym_scratch(const psfsim_plan *h, int B);
+cudaError_t psfsim_launch_forward_sym(const psfsim_plan *h, const float *x, int B, float *y, void *scratch,
+                                      cudaStream_t st);
+size_t psfsim_adjoint_sym_scratch(const psfsim_plan *h, int B);
+cudaError_t psfsim_launch_adjoint_sym(const psfsim_plan *h, const float *g, int B, float *gx, void *scratch,
+                                      cudaStream_t st);
 // Fused (A regenerated on chip) forward.
 size_t psfsim_forward_fused_scratch(const psfsim_plan *h, int B);
 cudaError_t psfsim_launch_forward_fused(const psfsim_plan *h, const float *x, int B, float *y, void *scratch,

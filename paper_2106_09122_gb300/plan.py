@@ -12,7 +12,7 @@ import torch
 
 from . import _binding as B
 
-_STORAGE = {"fp32": B.FP32, "split_bf16": B.SPLIT_BF16, "fused": B.FUSED}
+_STORAGE = {"fp32": B.FP32, "split_bf16": B.SPLIT_BF16, "fp32_sym": B.FP32_SYM, "fused": B.FUSED}
 _INTERP = {"linear": B.LINEAR, "nearest": B.NEAREST}
 
 

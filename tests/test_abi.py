@@ -81,8 +81,9 @@ def test_build_rejects_bad_arguments_before_launch(lib):
     assert h.value is None
 
 
-def test_fused_needs_an_even_scene_grid(lib):
+def test_symmetric_storages_need_an_even_scene_grid(lib):
     assert _build(lib, [0.0, 1.0, 2.0], N=9, storage=B.FUSED)[0] == B.ERR_UNSUPPORTED
+    assert _build(lib, [0.0, 1.0, 2.0], N=9, storage=B.FP32_SYM)[0] == B.ERR_UNSUPPORTED
 
 
 def test_products_reject_null_handles(lib):
