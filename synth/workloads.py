@@ -69,6 +69,27 @@ def fused_512() -> Workload:
                     r_max=12.0, seed=BASE_SEED + 4, extra={"scenes": 32})
 
 
+def ipac_shape() -> Workload:
+    """The paper's IPAC geometry (Sec. 2, Eq. 1): 85 PSFs of 128^2 at 0.2 lambda/D with offsets
+    sampled every 0.06 lambda/D to 4, 0.5 to 9 and 0.25 to 11 lambda/D; a 256^2 scene at
+    3.529 mas = 0.0703 lambda/D per pixel (A = 16384 x 65536)."""
+    radii = np.unique(np.round(np.concatenate([np.arange(0.0, 4.0, 0.06), np.arange(4.0, 9.0, 0.5),
+                                               np.arange(9.0, 11.0001, 0.25)]), 6))
+    mas_per_ld = 575e-9 / 2.3631 * 180.0 / np.pi * 3600e3
+    return Workload("ipac_shape_128_to_256", 128, 0.2, 256, 3.529 / mas_per_ld, radii, r_max=9.0,
+                    seed=BASE_SEED + 6)
+
+
+def powerlaw_disk_scene(N: int, S: float, r_max: float, alpha: float = 1.34, r_in: float = 0.5) -> np.ndarray:
+    """Smooth face-on dust disk with surface brightness ~ r^-alpha (the ZODIPIC default alpha of
+    Sec. 2), 1e-9 at 1 lambda/D, masked beyond r_max and inside r_in."""
+    X, Y = scenes.pixel_centres(N, S)
+    r = np.hypot(X, Y)
+    img = 1e-9 * np.power(np.maximum(r, r_in), -alpha)
+    img[(r > r_max) | (r < r_in)] = 0.0
+    return img
+
+
 def uneven_buckets() -> list[tuple[int, float]]:
     return [(N, S) for N in (64, 96, 128, 192, 256) for S in (0.3, 0.5)]
 

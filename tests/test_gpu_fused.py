@@ -68,3 +68,19 @@ def test_fused_512_crop_against_oracle_and_stored_path():
     Ys = stored.forward(torch.from_numpy(np.ascontiguousarray(X[:, cols])).to(DEV))
     torch.cuda.synchronize()
     assert float((Ys - Y).abs().max() / Y.abs().max()) <= TOL
+
+
+def test_fused_with_nonuniform_radii():
+    """IPAC-like offset sampling (dense near the centre, sparse further out)."""
+    rng = np.random.default_rng(91)
+    n, N, S = 28, 24, 0.25
+    radii = np.unique(np.concatenate([np.arange(0.0, 1.5, 0.06), np.arange(1.5, 3.0, 0.5), [3.0, 3.25, 3.5]]))
+    lib32 = rng.uniform(0.0, 1.0, (len(radii), n, n)).astype(np.float32)
+    plan = _plan(lib32, radii, 0.25, N=N, S=S, storage="fused")
+    A = O.build_A(lib32.astype(np.float64), radii, N, S)
+    x = rng.uniform(0.0, 1.0, (5, N * N)).astype(np.float32)
+    y = plan.forward(torch.from_numpy(x).to(DEV)).double().cpu().numpy()
+    for b in range(5):
+        x64 = x[b].astype(np.float64)
+        rel = O.bound_relative_error(y[b], A @ x64, np.abs(A) @ np.abs(x64), floor=O.FLT_MIN)
+        assert rel.max() <= TOL, rel.max()
