@@ -55,7 +55,6 @@ int common_build(const float *d_lib, const double *h_radii, int n_r, int n, doub
   h->S = S;
   h->quadrant = quadrant;
   h->Kg = h->quadrant ? K / 4 : K;
-  h->s = s;
   h->d_lib = d_lib;
   for (int i = 0; i < n_r; ++i) h->radii[i] = h_radii[i];
   h->ws = static_cast<char *>(d_ws);

@@ -365,7 +365,6 @@ cudaError_t psfsim_launch_build(psfsim_plan *h, cudaStream_t st) {
   const size_t smem = 2ull * (size_t)(n + 2) * Wp * 4;
   const bool vec4 = (n % 4) == 0;
   const bool use_smem = vec4 && smem <= 200 * 1024 && Wp <= 256 && encode_library_map(h, Wp);
-  h->lib_map_ok = use_smem;
   BuildParams P;
   P.n = n;
   P.n_r = h->n_r;

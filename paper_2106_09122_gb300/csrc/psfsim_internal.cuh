@@ -33,14 +33,13 @@ struct psfsim_plan {
   bool quadrant;  // FUSED: columns are the x > 0, y > 0 quadrant of the N x N grid
   int64_t Kg;     // columns with geometry tables (K, or K/4 for the quadrant)
   int64_t K_valid;  // FUSED: columns inside the last radius (host copy, read back at build)
-  double S, s;
+  double S;
   const float *d_lib;
   double radii[PSFSIM_MAX_RADII];
   char *ws;
   size_t ws_bytes;
   int64_t a_off, lo_off, scale_off, geom_off, order_off, bstart_off, pts_off, status_off, libmax_off, plib_off;
   int device, num_sms;
-  bool lib_map_ok;
   CUtensorMap lib_map;  // 3D tensor map over the library for TMA staging
 };
 
@@ -95,8 +94,3 @@ cudaError_t psfsim_launch_adjoint_split(const psfsim_plan *h, const float *g, in
 
 static inline int64_t psfsim_round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
-#define PSFSIM_CUDA_TRY(expr)                 \
-  do {                                        \
-    cudaError_t _e = (expr);                  \
-    if (_e != cudaSuccess) return PSFSIM_ERR_CUDA; \
-  } while (0)
