@@ -44,6 +44,7 @@ constexpr uint32_t kTileBytes = BM * BK * 2;
 // (p0 + r / 16, q0 + r % 16)), so a warp's 32 rows form a 16 x 2 patch and its
 // bilinear taps touch few cache lines.
 constexpr int kBlockQ = 16, kBlockP = 8;
+constexpr int kTabTiles = 4;  // k-tiles per column table (one generator barrier per table)
 
 struct FusedParams {
   int n, N, Bp, B, KS, m_tiles, k_tiles, stages, tiles_q;
@@ -58,11 +59,38 @@ struct FusedParams {
 
 // Per-column constants of one k-tile, shared by the generator warps: the
 // fixed-point source coordinates of the tile's origin pixel and the steps.
+// The steps C = cos and S = sin (fixed point) are kept as (lo, hi) 32-bit
+// pieces so that offsets u >= 0 inside a tile cost one wide and one narrow
+// integer multiply-add each (exact modulo 2^64).
 struct ColEntry {
-  long long A0, B0, C, S;
-  int64_t off;  // offset of L[k] in the padded library, or -1 for padding columns
+  long long A0, B0;
+  uint32_t Clo, Slo, NSlo;
+  int32_t Chi, Shi, NShi;
+  int64_t off;  // offset of L[k] in the quad-layout library, or -1 for padding columns
   float w0, w1;
 };
+
+__device__ __forceinline__ long long fx_mad(long long base, uint32_t lo, int32_t hi, uint32_t u) {
+  uint64_t r = (uint64_t)base + (uint64_t)lo * u;
+  r += (uint64_t)(uint32_t)(hi * (int32_t)u) << 32;
+  return (long long)r;
+}
+
+__device__ __forceinline__ void split64(long long v, uint32_t &lo, int32_t &hi) {
+  lo = (uint32_t)(unsigned long long)v;
+  hi = (int32_t)(v >> 32);
+}
+
+// The two bilinear weights of one axis from the 32-bit fixed-point fraction:
+// the smaller one is converted (relative accuracy 2^-24), the larger one is
+// 1 - smaller, exact because the smaller is at most 1/2.
+__device__ __forceinline__ void axis_weights(unsigned f, float &w_lo_tap, float &w_hi_tap) {
+  const bool low = f <= 0x80000000u;
+  const float small = __uint2float_rn(low ? f : 0u - f) * 2.3283064365386963e-10f;
+  const float large = 1.f - small;
+  w_hi_tap = low ? small : large;
+  w_lo_tap = low ? large : small;
+}
 
 // Library in "quad" layout: for every padded pixel (p, q), p, q in [-1, n-1],
 // the float4 (L[p][q], L[p][q+1], L[p+1][q], L[p+1][q+1]) with zeros outside
@@ -113,20 +141,16 @@ __global__ void fused_xgather(const float *__restrict__ x, int B, int Bp, int N,
 // offset from the tile origin.  The 2 x 2 footprint of each PSF is one float4
 // of the quad-layout library, so only the footprint position needs a check.
 __device__ __forceinline__ float gen_element(const ColEntry &e, const float4 *__restrict__ qlib, int n,
-                                             int64_t qsz, int du2, int dv2) {
+                                             int64_t qsz, uint32_t du2, uint32_t dv2) {
   constexpr int kShift = PSFSIM_FRAC_BITS + 1;
-  const long long a2 = e.A0 + e.C * du2 + e.S * dv2;
-  const long long b2 = e.B0 - e.S * du2 + e.C * dv2;
+  const long long a2 = fx_mad(fx_mad(e.A0, e.Clo, e.Chi, du2), e.Slo, e.Shi, dv2);
+  const long long b2 = fx_mad(fx_mad(e.B0, e.NSlo, e.NShi, du2), e.Clo, e.Chi, dv2);
   const int q0 = (int)(a2 >> kShift);
   const int p0 = (int)(b2 >> kShift);
   if (e.off < 0 || q0 < -1 || q0 > n - 1 || p0 < -1 || p0 > n - 1) return 0.f;
-  const unsigned fa = (unsigned)((unsigned long long)a2 >> (kShift - 32));
-  const unsigned fb = (unsigned)((unsigned long long)b2 >> (kShift - 32));
-  constexpr float kInv32 = 2.3283064365386963e-10f;
-  const float wa1 = __uint2float_rn(fa) * kInv32;
-  const float wa0 = fa ? __uint2float_rn(0u - fa) * kInv32 : 1.f;
-  const float wb1 = __uint2float_rn(fb) * kInv32;
-  const float wb0 = fb ? __uint2float_rn(0u - fb) * kInv32 : 1.f;
+  float wa0, wa1, wb0, wb1;
+  axis_weights((unsigned)((unsigned long long)a2 >> (kShift - 32)), wa0, wa1);
+  axis_weights((unsigned)((unsigned long long)b2 >> (kShift - 32)), wb0, wb1);
   const float4 *Q0 = qlib + e.off + (int64_t)(p0 + 1) * (n + 1) + (q0 + 1);
   const float4 t0 = __ldg(Q0);
   const float v0 = wb0 * (wa0 * t0.x + wa1 * t0.y) + wb1 * (wa0 * t0.z + wa1 * t0.w);
@@ -185,7 +209,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ __align__(8) uint64_t xfull[kMaxStages], gfull[kMaxStages], empty[kMaxStages], tfull[2], tempty[2];
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
-  __shared__ ColEntry ctab[2][BK];
+  __shared__ ColEntry ctab[2][kTabTiles * BK];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < P.stages; ++s) {
@@ -285,8 +309,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int n = P.n;
     const long long h = n - 1;
     const long long base = h << PSFSIM_FRAC_BITS;
-    const int du2 = 2 * (r % kBlockQ), dv2 = 2 * (r / kBlockQ);
-    uint32_t it = 0, c = 0;
+    const uint32_t du2 = 2 * (r % kBlockQ), dv2 = 2 * (r / kBlockQ);
+    uint32_t it = 0, c = 0, tg = 0;
+    const ColEntry *cur = ctab[0];
     bool ok = true;
     for (int u = blockIdx.x; u < units; u += gridDim.x) {
       const int ks = u / P.m_tiles, mt = u % P.m_tiles;
@@ -325,30 +350,40 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int kc = k0; kc < k1 && !stop; kc += kChunk, ++c) {
         const int kc1 = min(kc + kChunk, k1);
         for (int kt = kc; kt < kc1; ++kt, ++it) {
-          // Column table for this k-tile (double-buffered; one named barrier per tile).
-          ColEntry *tab = ctab[kt & 1];
-          if (gtid < BK) {
-            const int64_t t = (int64_t)kt * BK + gtid;
-            ColEntry e;
-            e.off = -1;
-            e.A0 = e.B0 = e.C = e.S = 0;
-            e.w0 = e.w1 = 0.f;
-            if (t < P.K0v) {
-              const ColGeom gm = P.geom[P.order[t]];
-              e.C = gm.C;
-              e.S = gm.Sn;
-              e.A0 = base + gm.C * uo + gm.Sn * vo;
-              e.B0 = base - gm.Sn * uo + gm.C * vo;
-              e.off = (int64_t)gm.k * P.psz;
-              e.w0 = gm.w0;
-              e.w1 = gm.w1;
+          // Column table for the next kTabTiles k-tiles (double-buffered; one
+          // named barrier per table, which also carries the abort decision).
+          if (((kt - k0) % kTabTiles) == 0) {
+            ColEntry *tab = ctab[tg & 1];
+            for (int c = gtid; c < kTabTiles * BK; c += kGenWarps * 32) {
+              const int64_t t = (int64_t)kt * BK + c;
+              ColEntry e;
+              e.off = -1;
+              e.A0 = e.B0 = 0;
+              e.Clo = e.Slo = e.NSlo = 0;
+              e.Chi = e.Shi = e.NShi = 0;
+              e.w0 = e.w1 = 0.f;
+              if (t < P.K0v && kt + c / BK < k1) {
+                const ColGeom gm = P.geom[P.order[t]];
+                e.A0 = base + gm.C * uo + gm.Sn * vo;
+                e.B0 = base - gm.Sn * uo + gm.C * vo;
+                split64(gm.C, e.Clo, e.Chi);
+                split64(gm.Sn, e.Slo, e.Shi);
+                split64(-gm.Sn, e.NSlo, e.NShi);
+                e.off = (int64_t)gm.k * P.psz;
+                e.w0 = gm.w0;
+                e.w1 = gm.w1;
+              }
+              tab[c] = e;
             }
-            tab[gtid] = e;
+            if (!gen_barrier_and(ok)) {
+              stop = true;
+              break;
+            }
+            cur = tab;
+            ++tg;
           }
-          if (!gen_barrier_and(ok)) {
-            stop = true;
-            break;
-          }
+          if (!ok) continue;  // after a timeout: no more work until the next barrier exits
+          const ColEntry *tab = cur + ((kt - k0) % kTabTiles) * BK;
           const int s = (int)(it % P.stages);
           if (!warp_wait(&empty[s], ((it / P.stages) & 1) ^ 1, &abort_flag, P.status)) {
             ok = false;
