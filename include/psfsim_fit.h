@@ -24,6 +24,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "psfsim.h"
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -44,6 +46,27 @@ int psfsim_ring_chain(int N, double S, double r_max, const double *h_theta, cons
  * not NULL, d_r[i] = (y_i - d_i)/sigma^2 (float32), the dL/dS the adjoint needs. */
 int psfsim_residual_loss(const float *d_y, const float *d_d, int64_t M, double sigma, float *d_r,
                          double *d_loss, void *d_scratch, size_t scratch_bytes, void *stream);
+
+/* One whole fit gradient on an FP32 grid plan, in six launches: the ring
+ * scene (d_z) with its parameter Jacobian, S = A Z (d_y) with the residual
+ * r = (S - d)/sigma^2 (d_r) and FP64 loss partials formed in the same
+ * reduction, A^T r (d_gz), the chain sums against the stored Jacobian, and one
+ * final sum: d_out (device double[6]) = {L, dL/dR, dL/dw, dL/di, dL/dg, dL/dB}.
+ * The scene grid (N, S) is the plan's.  Same quantities as psfsim_ring_scene
+ * + psfsim_forward + psfsim_residual_loss + psfsim_adjoint + psfsim_ring_chain.
+ * PSFSIM_ERR_UNSUPPORTED for other storages or point builds.  The two halves
+ * are also callable on their own (same scratch, same theta, in this order):
+ * the first leaves the loss partials and dZ/dtheta in the scratch for the
+ * second. */
+int psfsim_ring_gradient_scratch_bytes(psfsim_t h, size_t *bytes);
+int psfsim_ring_forward_loss(psfsim_t h, double r_max, const double *h_theta, const float *d_target, double sigma,
+                             float *d_z, float *d_y, float *d_r, void *d_scratch, size_t scratch_bytes,
+                             void *stream);
+int psfsim_ring_adjoint_chain(psfsim_t h, double r_max, const double *h_theta, const float *d_r, float *d_gz,
+                              double *d_out, void *d_scratch, size_t scratch_bytes, void *stream);
+int psfsim_ring_gradient(psfsim_t h, double r_max, const double *h_theta, const float *d_target, double sigma,
+                         float *d_z, float *d_y, float *d_r, float *d_gz, double *d_out, void *d_scratch,
+                         size_t scratch_bytes, void *stream);
 
 #ifdef __cplusplus
 }

@@ -57,6 +57,10 @@ SIGNATURES = {
     "psfsim_ring_scene": (i32, [i32, f64, f64, vp, vp, vp]),
     "psfsim_ring_chain": (i32, [i32, f64, f64, vp, vp, vp, vp, ctypes.c_size_t, vp]),
     "psfsim_residual_loss": (i32, [vp, vp, i64, f64, vp, vp, vp, ctypes.c_size_t, vp]),
+    "psfsim_ring_gradient_scratch_bytes": (i32, [vp, c_size_p]),
+    "psfsim_ring_gradient": (i32, [vp, f64, vp, vp, f64, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]),
+    "psfsim_ring_forward_loss": (i32, [vp, f64, vp, vp, f64, vp, vp, vp, vp, ctypes.c_size_t, vp]),
+    "psfsim_ring_adjoint_chain": (i32, [vp, f64, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]),
     "psfsim_free": (None, [vp]),
 }
 

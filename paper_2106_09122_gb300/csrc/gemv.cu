@@ -107,6 +107,53 @@ __global__ void __launch_bounds__(256) fwd_reduce_kernel(const float *__restrict
   }
 }
 
+// One image: y[i] = sum_ks part[ks][i] (fixed order) fused with the fit's
+// residual r = (y - d) / sigma^2 and FP64 loss partials sum ((y - d)/sigma)^2
+// per block (same layout as fwd_reduce_kernel, 128 rows per CTA).
+__global__ void __launch_bounds__(256) fwd_reduce_loss_kernel(const float *__restrict__ part, int KS, int64_t ld,
+                                                              int64_t M, const float *__restrict__ d, double sigma,
+                                                              float inv_s2, float *__restrict__ y,
+                                                              float *__restrict__ r, double *__restrict__ loss_part) {
+  __shared__ float4 red[8][32];
+  const int c4 = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  const int64_t row = ((int64_t)blockIdx.x * 32 + c4) * 4;
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (row < ld) {
+#pragma unroll 4
+    for (int ks = grp; ks < KS; ks += 8) {
+      const float4 v = *reinterpret_cast<const float4 *>(part + (int64_t)ks * ld + row);
+      s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+    }
+  }
+  red[grp][c4] = s;
+  __syncthreads();
+  if (grp == 0) {
+    double acc = 0.0;
+    if (row < M) {
+      float4 t = red[0][c4];
+#pragma unroll
+      for (int k = 1; k < 8; ++k) {
+        const float4 v = red[k][c4];
+        t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w;
+      }
+      const float vals[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (row + e < M) {
+          y[row + e] = vals[e];
+          const float diff = vals[e] - d[row + e];
+          r[row + e] = diff * inv_s2;
+          const double q = (double)diff / sigma;
+          acc += q * q;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (c4 == 0) loss_part[blockIdx.x] = acc;
+  }
+}
+
 int forward_splits(const psfsim_plan *h) {
   const int64_t row_blocks = (h->ld + kRowsPerCta - 1) / kRowsPerCta;
   int64_t ks = (int64_t)h->num_sms * 8 / row_blocks;
@@ -263,6 +310,19 @@ cudaError_t psfsim_launch_adjoint_cols(const float *A, int64_t ld, int64_t M, in
     b0 += bb;
   }
   return cudaSuccess;
+}
+
+int psfsim_reduce_loss_blocks(const psfsim_plan *h) { return (int)((h->ld + kRedRows - 1) / kRedRows); }
+
+cudaError_t psfsim_launch_forward_loss(const psfsim_plan *h, const float *x, const float *d, double sigma, float *y,
+                                       float *r, void *scratch, double *loss_part, cudaStream_t st) {
+  const int KS = forward_splits(h);
+  float *part = reinterpret_cast<float *>(scratch);
+  cudaError_t e = fwd_group<1>(h, x, 1, 0, part, KS, st);
+  if (e != cudaSuccess) return e;
+  fwd_reduce_loss_kernel<<<psfsim_reduce_loss_blocks(h), 256, 0, st>>>(part, KS, h->ld, h->M, d, sigma,
+                                                                       (float)(1.0 / (sigma * sigma)), y, r, loss_part);
+  return cudaGetLastError();
 }
 
 size_t psfsim_forward_fp32_scratch(const psfsim_plan *h, int B) {

@@ -72,6 +72,10 @@ int psfsim_multi_validate(const psfsim_job_t *jobs, int njobs);
 size_t psfsim_forward_multi_scratch(const psfsim_job_t *jobs, int njobs, const psfsim_tuning_t *tune);
 cudaError_t psfsim_launch_forward_multi(const psfsim_job_t *jobs, int njobs, const psfsim_tuning_t *tune,
                                         void *scratch, cudaStream_t st);
+// Fit gradient on FP32 storage: forward fused with the residual and loss partials.
+int psfsim_reduce_loss_blocks(const psfsim_plan *h);
+cudaError_t psfsim_launch_forward_loss(const psfsim_plan *h, const float *x, const float *d, double sigma, float *y,
+                                       float *r, void *scratch, double *loss_part, cudaStream_t st);
 // Generic FP32 GEMV pieces (column-major A) used by several storages.
 int psfsim_gemv_splits(int64_t ld, int64_t K, int num_sms);
 cudaError_t psfsim_launch_gemv_partials(const float *A, int64_t ld, int64_t K, const float *x, int B, float *part,

@@ -6,62 +6,22 @@
 
 #include "../../include/psfsim_fit.h"
 #include "psfsim_internal.cuh"
+#include "ring_model.cuh"
 
 namespace {
 
 constexpr int kRedBlocks = 256;
 constexpr int kRedThreads = 256;
 
-struct RingParams {
-  int N;
-  double S, r_max;
-  float R, w, inc, g, B;
-};
-
-// Z_j and (optionally) dZ_j/d(R, w, i, g, B) for scene pixel j.
-template <bool kJac>
-__device__ __forceinline__ float ring_eval(const RingParams &P, int64_t j, float *J) {
-  const int iy = (int)(j / P.N), ix = (int)(j % P.N);
-  const double half = 0.5 * (double)(P.N - 1);
-  const double xs = __dmul_rn((double)ix - half, P.S), ys = __dmul_rn((double)iy - half, P.S);
-  const bool inside = __dsqrt_rn(__dadd_rn(__dmul_rn(xs, xs), __dmul_rn(ys, ys))) <= P.r_max;
-  if (!inside) {
-    if (kJac)
-      for (int m = 0; m < 5; ++m) J[m] = 0.f;
-    return 0.f;
+// Scene and its parameter Jacobian, jac[m * K + j] = dZ_j / dtheta_m.
+__global__ void ring_scene_jac_kernel(const RingParams P, float *z, float *jac) {
+  const int64_t K = (int64_t)P.N * P.N;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < K; j += (int64_t)gridDim.x * blockDim.x) {
+    float J[5];
+    z[j] = ring_eval<true>(P, j, J);
+#pragma unroll
+    for (int m = 0; m < 5; ++m) jac[m * K + j] = J[m];
   }
-  const float x = (float)xs, y = (float)ys;
-  float si, ci;
-  sincosf(P.inc, &si, &ci);
-  const float yd = y / ci;
-  const float rd = sqrtf(x * x + yd * yd);
-  const bool pos = rd > 0.f;
-  const float mu = pos ? si * yd / rd : 0.f;
-  const float alpha = 2.7725887222397811f;  // 4 ln 2
-  const float dr = rd - P.R;
-  const float w2 = P.w * P.w;
-  const float G = expf(-alpha * dr * dr / w2);
-  const float g2 = 1.f + P.g * P.g;
-  const float den = g2 - 2.f * P.g * mu;
-  const float ratio = g2 / den;
-  const float H = ratio * sqrtf(ratio);
-  const float z = P.B * G * H;
-  if (kJac) {
-    const float dyd_di = yd * si / ci;
-    const float drd_di = pos ? yd * dyd_di / rd : 0.f;
-    const float dmu_di = pos ? ci * yd / rd + si * (dyd_di * rd - yd * drd_di) / (rd * rd) : 0.f;
-    const float dG_dR = G * 2.f * alpha * dr / w2;
-    const float dG_dw = G * 2.f * alpha * dr * dr / (w2 * P.w);
-    const float dG_di = -dG_dR * drd_di;
-    const float dH_dmu = 3.f * P.g * H / den;
-    const float dH_dg = H * 1.5f * (2.f * P.g / g2 - (2.f * P.g - 2.f * mu) / den);
-    J[0] = P.B * dG_dR * H;
-    J[1] = P.B * dG_dw * H;
-    J[2] = P.B * (dG_di * H + G * dH_dmu * dmu_di);
-    J[3] = P.B * G * dH_dg;
-    J[4] = G * H;
-  }
-  return z;
 }
 
 __global__ void ring_scene_kernel(const RingParams P, float *z) {
@@ -133,6 +93,50 @@ __global__ void __launch_bounds__(kRedThreads) loss_partial(const float *y, cons
   if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
 }
 
+// dL/dtheta_m partials: sum_j gz[j] * jac[m * K + j] over a fixed grid (FP64).
+__global__ void __launch_bounds__(kRedThreads) chain_dot_partial(const float *gz, const float *jac, int64_t K,
+                                                                double *part) {
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < K; j += (int64_t)gridDim.x * blockDim.x) {
+    const double gj = (double)gz[j];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) acc[m] += gj * (double)jac[m * K + j];
+  }
+  block_reduce<5>(acc);
+  if (threadIdx.x == 0)
+    for (int m = 0; m < 5; ++m) part[blockIdx.x * 5 + m] = acc[m];
+}
+
+constexpr int kChainBlocks = 64;
+
+__global__ void __launch_bounds__(kRedThreads) finish_gradient(const double *loss_part, int nl,
+                                                              const double *chain_part, int nc, double *out) {
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nl; b += blockDim.x) acc[0] += loss_part[b];
+  for (int b = threadIdx.x; b < nc; b += blockDim.x)
+#pragma unroll
+    for (int m = 0; m < 5; ++m) acc[1 + m] += chain_part[b * 5 + m];
+  block_reduce<6>(acc);
+  if (threadIdx.x == 0) {
+    out[0] = 0.5 * acc[0];
+    for (int m = 0; m < 5; ++m) out[1 + m] = acc[1 + m];
+  }
+}
+
+struct GradScratch {
+  size_t part, loss, chain, jac, total;
+};
+
+GradScratch gradient_scratch(const psfsim_plan *h) {
+  GradScratch g;
+  g.part = 0;
+  g.loss = (size_t)psfsim_round_up((int64_t)psfsim_forward_fp32_scratch(h, 1), 256);
+  g.chain = g.loss + (size_t)psfsim_round_up((int64_t)psfsim_reduce_loss_blocks(h) * 8, 256);
+  g.jac = g.chain + (size_t)psfsim_round_up((int64_t)kChainBlocks * 5 * 8, 256);
+  g.total = g.jac + (size_t)5 * h->K * 4;
+  return g;
+}
+
 bool ring_params(int N, double S, double r_max, const double *th, RingParams *P) {
   if (N < 1 || N > 32768 || !(S > 0.0) || !th || !(r_max >= 0.0)) return false;
   for (int m = 0; m < 5; ++m)
@@ -199,6 +203,70 @@ int psfsim_residual_loss(const float *d_y, const float *d_d, int64_t M, double s
   loss_partial<<<kRedBlocks, kRedThreads, 0, st>>>(d_y, d_d, M, sigma, (float)(1.0 / (sigma * sigma)), d_r, part);
   finish_sum<1><<<1, kRedThreads, 0, st>>>(part, kRedBlocks, 0.5, d_loss);
   return cudaGetLastError() == cudaSuccess ? PSFSIM_OK : PSFSIM_ERR_CUDA;
+}
+
+int psfsim_ring_gradient_scratch_bytes(psfsim_t h, size_t *bytes) {
+  if (!h || !bytes) return PSFSIM_ERR_ARG;
+  if (h->storage != PSFSIM_FP32 || h->N < 1) return PSFSIM_ERR_UNSUPPORTED;
+  *bytes = gradient_scratch(h).total;
+  return PSFSIM_OK;
+}
+
+static int gradient_args(psfsim_t h, double r_max, const double *h_theta, void *d_scratch, size_t scratch_bytes,
+                         RingParams *P, GradScratch *g) {
+  if (!h) return PSFSIM_ERR_ARG;
+  if (h->storage != PSFSIM_FP32 || h->N < 1) return PSFSIM_ERR_UNSUPPORTED;
+  if (!ring_params(h->N, h->S, r_max, h_theta, P)) return PSFSIM_ERR_ARG;
+  *g = gradient_scratch(h);
+  if (!d_scratch || !aligned256(d_scratch) || scratch_bytes < g->total) return PSFSIM_ERR_WORKSPACE;
+  return PSFSIM_OK;
+}
+
+int psfsim_ring_forward_loss(psfsim_t h, double r_max, const double *h_theta, const float *d_target, double sigma,
+                             float *d_z, float *d_y, float *d_r, void *d_scratch, size_t scratch_bytes,
+                             void *stream) {
+  if (!d_target || !d_z || !d_y || !d_r || !(sigma > 0.0) || !std::isfinite(sigma)) return PSFSIM_ERR_ARG;
+  RingParams P;
+  GradScratch g;
+  if (int rc = gradient_args(h, r_max, h_theta, d_scratch, scratch_bytes, &P, &g)) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char *base = static_cast<char *>(d_scratch);
+  const int64_t K = (int64_t)h->N * h->N;
+  ring_scene_jac_kernel<<<(unsigned)((K + 255) / 256 < 4096 ? (K + 255) / 256 : 4096), 256, 0, st>>>(
+      P, d_z, reinterpret_cast<float *>(base + g.jac));
+  if (cudaGetLastError() != cudaSuccess) return PSFSIM_ERR_CUDA;
+  return psfsim_launch_forward_loss(h, d_z, d_target, sigma, d_y, d_r, base + g.part,
+                                    reinterpret_cast<double *>(base + g.loss), st) == cudaSuccess
+             ? PSFSIM_OK
+             : PSFSIM_ERR_CUDA;
+}
+
+int psfsim_ring_adjoint_chain(psfsim_t h, double r_max, const double *h_theta, const float *d_r, float *d_gz,
+                              double *d_out, void *d_scratch, size_t scratch_bytes, void *stream) {
+  if (!d_r || !d_gz || !d_out) return PSFSIM_ERR_ARG;
+  RingParams P;
+  GradScratch g;
+  if (int rc = gradient_args(h, r_max, h_theta, d_scratch, scratch_bytes, &P, &g)) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char *base = static_cast<char *>(d_scratch);
+  double *chain_part = reinterpret_cast<double *>(base + g.chain);
+  if (psfsim_launch_adjoint_cols(reinterpret_cast<const float *>(h->ws + h->a_off), h->ld, h->M, h->K, d_r, 1, d_gz,
+                                 h->num_sms, st) != cudaSuccess)
+    return PSFSIM_ERR_CUDA;
+  chain_dot_partial<<<kChainBlocks, kRedThreads, 0, st>>>(d_gz, reinterpret_cast<const float *>(base + g.jac), h->K,
+                                                          chain_part);
+  finish_gradient<<<1, kRedThreads, 0, st>>>(reinterpret_cast<const double *>(base + g.loss),
+                                             psfsim_reduce_loss_blocks(h), chain_part, kChainBlocks, d_out);
+  return cudaGetLastError() == cudaSuccess ? PSFSIM_OK : PSFSIM_ERR_CUDA;
+}
+
+int psfsim_ring_gradient(psfsim_t h, double r_max, const double *h_theta, const float *d_target, double sigma,
+                         float *d_z, float *d_y, float *d_r, float *d_gz, double *d_out, void *d_scratch,
+                         size_t scratch_bytes, void *stream) {
+  int rc = psfsim_ring_forward_loss(h, r_max, h_theta, d_target, sigma, d_z, d_y, d_r, d_scratch, scratch_bytes,
+                                    stream);
+  if (rc != PSFSIM_OK) return rc;
+  return psfsim_ring_adjoint_chain(h, r_max, h_theta, d_r, d_gz, d_out, d_scratch, scratch_bytes, stream);
 }
 
 }  // extern "C"

@@ -48,6 +48,10 @@ class RingProblem:
         self.cscr = torch.empty(nb.value, **u8)
         B.check(self.lib.psfsim_loss_scratch_bytes(plan.M, ctypes.byref(nb)), "loss scratch")
         self.lscr = torch.empty(nb.value, **u8)
+        # FP32 grid plans take the fused path (six launches per gradient).
+        self.out6 = torch.empty(6, dtype=torch.float64, device=dev)
+        self.fused = self.lib.psfsim_ring_gradient_scratch_bytes(plan.handle, ctypes.byref(nb)) == B.OK
+        self.gscr = torch.empty(max(nb.value, 256), **u8) if self.fused else None
         self.launches = 0
 
     # -- operators ---------------------------------------------------------
@@ -81,13 +85,38 @@ class RingProblem:
         self.launches += 2
         self.residual_loss(self.y, self.target, False)
 
+    def enqueue_forward_loss(self, theta) -> None:
+        """First half: ring scene and Jacobian, S = A Z with residual and loss partials (FP32 grid plans)."""
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        B.check(self.lib.psfsim_ring_forward_loss(self.plan.handle, self.r_max, th.ctypes.data_as(ctypes.c_void_p),
+                                                  _vp(self.target), self.sigma, _vp(self.z), _vp(self.y), _vp(self.r),
+                                                  _vp(self.gscr), self.gscr.numel(), _stream_ptr(None)),
+                "psfsim_ring_forward_loss")
+        self.launches += 3
+
+    def enqueue_adjoint_chain(self, theta) -> None:
+        """Second half: A^T r, the chain sums against the stored Jacobian, the final sums into out6."""
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        B.check(self.lib.psfsim_ring_adjoint_chain(self.plan.handle, self.r_max, th.ctypes.data_as(ctypes.c_void_p),
+                                                   _vp(self.r), _vp(self.gz), _vp(self.out6), _vp(self.gscr),
+                                                   self.gscr.numel(), _stream_ptr(None)),
+                "psfsim_ring_adjoint_chain")
+        self.launches += 3
+
     def enqueue_gradient(self, theta) -> None:
-        """Ring -> forward -> loss and residual -> adjoint -> chain, all enqueued."""
+        """Ring -> forward -> loss and residual -> adjoint -> chain, all enqueued; the result lands
+        in out6 = (loss, dL/dtheta)."""
+        if self.fused:
+            self.enqueue_forward_loss(theta)
+            self.enqueue_adjoint_chain(theta)
+            return
         self.plan.forward(self.scene(theta), out=self.y, scratch=self.fscr)
         self.residual_loss(self.y, self.target, True)
         self.plan.adjoint(self.r, out=self.gz, scratch=self.ascr)
         self.launches += 3
         self.chain(theta, self.gz)
+        self.out6[:1].copy_(self.loss_d)
+        self.out6[1:].copy_(self.dtheta)
 
     def loss(self, theta) -> float:
         self.enqueue_loss(theta)
@@ -95,7 +124,7 @@ class RingProblem:
 
     def loss_and_grad(self, theta):
         self.enqueue_gradient(theta)
-        out = torch.cat([self.loss_d, self.dtheta]).cpu().numpy()
+        out = self.out6.cpu().numpy()
         return float(out[0]), out[1:].copy()
 
     def gauss_newton_diagonal(self, theta) -> np.ndarray:

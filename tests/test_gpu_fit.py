@@ -112,3 +112,22 @@ def test_adjoint_fit_workload_gradient_and_fit():
     assert np.all(np.diff(hist) <= 0.0)
     assert hist[-1] < 1e-3 * hist[0]
     assert np.all(np.abs(theta - truth) <= np.abs(theta0 - truth))
+
+
+def test_fused_gradient_equals_separate_operators():
+    """psfsim_ring_gradient (5 launches) against ring + forward + loss + adjoint + chain."""
+    w = workloads.adjoint_128()
+    lib32 = w.library().astype(np.float32)
+    truth = np.array(w.extra["truth"])
+    rng = np.random.default_rng(35)
+    d32 = (rng.uniform(0.5, 1.5, w.M) * 1e-10).astype(np.float32)
+    P = _problem(lib32, w.radii, w.s, w.N, w.S, w.r_max, d32, w.extra["sigma"])
+    assert P.fused
+    theta = truth * np.array([1.03, 0.95, 1.02, 1.1, 1.2])
+    loss_f, g_f = P.loss_and_grad(theta)
+    y_f = P.y.clone()
+    P.fused = False
+    loss_s, g_s = P.loss_and_grad(theta)
+    assert torch.allclose(P.y, y_f, rtol=1e-6, atol=0)
+    assert loss_f == pytest.approx(loss_s, rel=1e-6)
+    np.testing.assert_allclose(g_f, g_s, rtol=1e-5)
