@@ -38,8 +38,9 @@ class RingProblem:
         self.gz = torch.empty(plan.K, **f32)
         self.jac = torch.empty((5, plan.K), **f32)
         self.jy = torch.empty((5, plan.M), **f32)
-        self.dtheta = torch.empty(5, dtype=torch.float64, device=dev)
-        self.loss_d = torch.empty(1, dtype=torch.float64, device=dev)
+        # out6 = (loss, dL/dtheta); the separate operators write straight into its views.
+        self.out6 = torch.empty(6, dtype=torch.float64, device=dev)
+        self.loss_d, self.dtheta = self.out6[:1], self.out6[1:]
         u8 = dict(dtype=torch.uint8, device=dev)
         self.fscr = torch.empty(max(plan.forward_scratch_bytes(5), 1), **u8)
         self.ascr = torch.empty(max(plan.adjoint_scratch_bytes(1), 1), **u8)
@@ -49,7 +50,6 @@ class RingProblem:
         B.check(self.lib.psfsim_loss_scratch_bytes(plan.M, ctypes.byref(nb)), "loss scratch")
         self.lscr = torch.empty(nb.value, **u8)
         # FP32 grid plans take the fused path (six launches per gradient).
-        self.out6 = torch.empty(6, dtype=torch.float64, device=dev)
         self.fused = self.lib.psfsim_ring_gradient_scratch_bytes(plan.handle, ctypes.byref(nb)) == B.OK
         self.gscr = torch.empty(max(nb.value, 256), **u8) if self.fused else None
         self.launches = 0
@@ -115,8 +115,6 @@ class RingProblem:
         self.plan.adjoint(self.r, out=self.gz, scratch=self.ascr)
         self.launches += 3
         self.chain(theta, self.gz)
-        self.out6[:1].copy_(self.loss_d)
-        self.out6[1:].copy_(self.dtheta)
 
     def loss(self, theta) -> float:
         self.enqueue_loss(theta)
