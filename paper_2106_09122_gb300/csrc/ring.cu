@@ -13,8 +13,11 @@ namespace {
 constexpr int kRedBlocks = 256;
 constexpr int kRedThreads = 256;
 
-// Scene and its parameter Jacobian, jac[m * K + j] = dZ_j / dtheta_m.
-__global__ void ring_scene_jac_kernel(const RingParams P, float *z, float *jac) {
+// Scene and its parameter Jacobian, jac[m * K + j] = dZ_j / dtheta_m; block 0
+// also zeroes the arrival counters of the fused forward and adjoint that follow.
+__global__ void ring_scene_jac_kernel(const RingParams P, float *z, float *jac, unsigned *count, int n_count) {
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < n_count; i += blockDim.x) count[i] = 0u;
   const int64_t K = (int64_t)P.N * P.N;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < K; j += (int64_t)gridDim.x * blockDim.x) {
     float J[5];
@@ -93,46 +96,19 @@ __global__ void __launch_bounds__(kRedThreads) loss_partial(const float *y, cons
   if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
 }
 
-// dL/dtheta_m partials: sum_j gz[j] * jac[m * K + j] over a fixed grid (FP64).
-__global__ void __launch_bounds__(kRedThreads) chain_dot_partial(const float *gz, const float *jac, int64_t K,
-                                                                double *part) {
-  double acc[5] = {0, 0, 0, 0, 0};
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < K; j += (int64_t)gridDim.x * blockDim.x) {
-    const double gj = (double)gz[j];
-#pragma unroll
-    for (int m = 0; m < 5; ++m) acc[m] += gj * (double)jac[m * K + j];
-  }
-  block_reduce<5>(acc);
-  if (threadIdx.x == 0)
-    for (int m = 0; m < 5; ++m) part[blockIdx.x * 5 + m] = acc[m];
-}
-
-constexpr int kChainBlocks = 64;
-
-__global__ void __launch_bounds__(kRedThreads) finish_gradient(const double *loss_part, int nl,
-                                                              const double *chain_part, int nc, double *out) {
-  double acc[6] = {0, 0, 0, 0, 0, 0};
-  for (int b = threadIdx.x; b < nl; b += blockDim.x) acc[0] += loss_part[b];
-  for (int b = threadIdx.x; b < nc; b += blockDim.x)
-#pragma unroll
-    for (int m = 0; m < 5; ++m) acc[1 + m] += chain_part[b * 5 + m];
-  block_reduce<6>(acc);
-  if (threadIdx.x == 0) {
-    out[0] = 0.5 * acc[0];
-    for (int m = 0; m < 5; ++m) out[1 + m] = acc[1 + m];
-  }
-}
-
 struct GradScratch {
-  size_t part, loss, chain, jac, total;
+  size_t part, loss, chain, count, jac, total;
+  int n_count;  // forward slice counters, then the adjoint's counter
 };
 
 GradScratch gradient_scratch(const psfsim_plan *h) {
   GradScratch g;
+  g.n_count = psfsim_forward_loss_slices(h) + 1;
   g.part = 0;
-  g.loss = (size_t)psfsim_round_up((int64_t)psfsim_forward_fp32_scratch(h, 1), 256);
-  g.chain = g.loss + (size_t)psfsim_round_up((int64_t)psfsim_reduce_loss_blocks(h) * 8, 256);
-  g.jac = g.chain + (size_t)psfsim_round_up((int64_t)kChainBlocks * 5 * 8, 256);
+  g.loss = (size_t)psfsim_round_up((int64_t)psfsim_forward_loss_scratch(h), 256);
+  g.chain = g.loss + (size_t)psfsim_round_up((int64_t)psfsim_forward_loss_slices(h) * 8, 256);
+  g.count = g.chain + (size_t)psfsim_round_up((int64_t)psfsim_adjoint_chain_max_blocks(h) * 5 * 8, 256);
+  g.jac = g.count + (size_t)psfsim_round_up((int64_t)g.n_count * 4, 256);
   g.total = g.jac + (size_t)5 * h->K * 4;
   return g;
 }
@@ -232,11 +208,12 @@ int psfsim_ring_forward_loss(psfsim_t h, double r_max, const double *h_theta, co
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   char *base = static_cast<char *>(d_scratch);
   const int64_t K = (int64_t)h->N * h->N;
+  unsigned *count = reinterpret_cast<unsigned *>(base + g.count);
   ring_scene_jac_kernel<<<(unsigned)((K + 255) / 256 < 4096 ? (K + 255) / 256 : 4096), 256, 0, st>>>(
-      P, d_z, reinterpret_cast<float *>(base + g.jac));
+      P, d_z, reinterpret_cast<float *>(base + g.jac), count, g.n_count);
   if (cudaGetLastError() != cudaSuccess) return PSFSIM_ERR_CUDA;
   return psfsim_launch_forward_loss(h, d_z, d_target, sigma, d_y, d_r, base + g.part,
-                                    reinterpret_cast<double *>(base + g.loss), st) == cudaSuccess
+                                    reinterpret_cast<double *>(base + g.loss), count, st) == cudaSuccess
              ? PSFSIM_OK
              : PSFSIM_ERR_CUDA;
 }
@@ -249,15 +226,13 @@ int psfsim_ring_adjoint_chain(psfsim_t h, double r_max, const double *h_theta, c
   if (int rc = gradient_args(h, r_max, h_theta, d_scratch, scratch_bytes, &P, &g)) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   char *base = static_cast<char *>(d_scratch);
-  double *chain_part = reinterpret_cast<double *>(base + g.chain);
-  if (psfsim_launch_adjoint_cols(reinterpret_cast<const float *>(h->ws + h->a_off), h->ld, h->M, h->K, d_r, 1, d_gz,
-                                 h->num_sms, st) != cudaSuccess)
-    return PSFSIM_ERR_CUDA;
-  chain_dot_partial<<<kChainBlocks, kRedThreads, 0, st>>>(d_gz, reinterpret_cast<const float *>(base + g.jac), h->K,
-                                                          chain_part);
-  finish_gradient<<<1, kRedThreads, 0, st>>>(reinterpret_cast<const double *>(base + g.loss),
-                                             psfsim_reduce_loss_blocks(h), chain_part, kChainBlocks, d_out);
-  return cudaGetLastError() == cudaSuccess ? PSFSIM_OK : PSFSIM_ERR_CUDA;
+  return psfsim_launch_adjoint_chain(h, d_r, d_gz, reinterpret_cast<const float *>(base + g.jac),
+                                     reinterpret_cast<double *>(base + g.chain),
+                                     reinterpret_cast<const double *>(base + g.loss),
+                                     reinterpret_cast<unsigned *>(base + g.count) + g.n_count - 1, d_out,
+                                     st) == cudaSuccess
+             ? PSFSIM_OK
+             : PSFSIM_ERR_CUDA;
 }
 
 int psfsim_ring_gradient(psfsim_t h, double r_max, const double *h_theta, const float *d_target, double sigma,

@@ -49,7 +49,7 @@ class RingProblem:
         self.cscr = torch.empty(nb.value, **u8)
         B.check(self.lib.psfsim_loss_scratch_bytes(plan.M, ctypes.byref(nb)), "loss scratch")
         self.lscr = torch.empty(nb.value, **u8)
-        # FP32 grid plans take the fused path (six launches per gradient).
+        # FP32 grid plans take the fused path (three launches per gradient).
         self.fused = self.lib.psfsim_ring_gradient_scratch_bytes(plan.handle, ctypes.byref(nb)) == B.OK
         self.gscr = torch.empty(max(nb.value, 256), **u8) if self.fused else None
         self.launches = 0
@@ -92,16 +92,16 @@ class RingProblem:
                                                   _vp(self.target), self.sigma, _vp(self.z), _vp(self.y), _vp(self.r),
                                                   _vp(self.gscr), self.gscr.numel(), _stream_ptr(None)),
                 "psfsim_ring_forward_loss")
-        self.launches += 3
+        self.launches += 2
 
     def enqueue_adjoint_chain(self, theta) -> None:
-        """Second half: A^T r, the chain sums against the stored Jacobian, the final sums into out6."""
+        """Second half: A^T r with the chain sums against the stored Jacobian and the final sums into out6."""
         th = np.ascontiguousarray(theta, dtype=np.float64)
         B.check(self.lib.psfsim_ring_adjoint_chain(self.plan.handle, self.r_max, th.ctypes.data_as(ctypes.c_void_p),
                                                    _vp(self.r), _vp(self.gz), _vp(self.out6), _vp(self.gscr),
                                                    self.gscr.numel(), _stream_ptr(None)),
                 "psfsim_ring_adjoint_chain")
-        self.launches += 3
+        self.launches += 1
 
     def enqueue_gradient(self, theta) -> None:
         """Ring -> forward -> loss and residual -> adjoint -> chain, all enqueued; the result lands

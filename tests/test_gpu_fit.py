@@ -115,7 +115,7 @@ def test_adjoint_fit_workload_gradient_and_fit():
 
 
 def test_fused_gradient_equals_separate_operators():
-    """psfsim_ring_gradient (5 launches) against ring + forward + loss + adjoint + chain."""
+    """psfsim_ring_gradient (3 launches) against ring + forward + loss + adjoint + chain."""
     w = workloads.adjoint_128()
     lib32 = w.library().astype(np.float32)
     truth = np.array(w.extra["truth"])
@@ -131,3 +131,34 @@ def test_fused_gradient_equals_separate_operators():
     assert torch.allclose(P.y, y_f, rtol=1e-6, atol=0)
     assert loss_f == pytest.approx(loss_s, rel=1e-6)
     np.testing.assert_allclose(g_f, g_s, rtol=1e-5)
+
+
+@pytest.mark.parametrize("n,N", [(21, 6), (48, 40), (33, 70)])
+def test_fused_gradient_on_ragged_shapes_repeats_and_matches_separate(n, N):
+    """Ragged row tiles (M = n^2 not a multiple of the 1024-row tile, odd M for the
+    scalar adjoint path), fewer columns than the forward's splits (K = 36), and
+    repeated calls: the arrival counters must be back at zero after every launch,
+    so a second gradient, and the adjoint half called twice, give identical bits."""
+    rng = np.random.default_rng(100 * n + N)
+    S = 0.3
+    radii = np.linspace(0.0, 6.0, 12)
+    lib32 = rng.uniform(0.0, 1e-3, (12, n, n)).astype(np.float32)
+    d32 = (rng.uniform(0.5, 1.5, n * n) * 1e-10).astype(np.float32)
+    half = N * S / 2
+    P = _problem(lib32, radii, S, N, S, 0.95 * half, d32, 1e-11)
+    assert P.fused
+    theta = np.array([half / 2, half / 3, np.deg2rad(50.0), 0.3, 1e-9])
+    loss_f, g_f = P.loss_and_grad(theta)
+    loss_f2, g_f2 = P.loss_and_grad(theta)
+    assert loss_f2 == loss_f and np.array_equal(g_f2, g_f)
+    y_f = P.y.clone()
+    P.enqueue_adjoint_chain(theta)
+    out_a = P.out6.cpu().numpy().copy()
+    P.enqueue_adjoint_chain(theta)
+    out_b = P.out6.cpu().numpy().copy()
+    assert np.array_equal(out_a, out_b) and out_a[0] == loss_f and np.array_equal(out_a[1:], g_f)
+    P.fused = False
+    loss_s, g_s = P.loss_and_grad(theta)
+    assert torch.allclose(P.y, y_f, rtol=1e-6, atol=0)
+    assert loss_f == pytest.approx(loss_s, rel=1e-6)
+    np.testing.assert_allclose(g_f, g_s, rtol=1e-5, atol=1e-6 * np.abs(g_s).max())
