@@ -268,7 +268,7 @@ def _gpu_arm(args, rank, world, local_rank):
         "data": "synthetic (seeded Lyot-coronagraph PSFs, exozodi ring scene)",
         "config": {"workload": f"{w.name}: n=N=128, s=S=0.25 lambda/D, 40 radii 0-12 lambda/D, "
                                "A 16384x16384 FP32; step = one fit gradient: ring Z(theta), S = A Z with residual "
-                               "and FP64 loss, A^T r with the chain to the 5 ring parameters (3 launches)",
+                               "and FP64 loss, A^T r with the chain to the 5 ring parameters (2 launches)",
                    "M": w.M, "K": w.K, "n_radii": len(w.radii), "storage": "fp32",
                    "l2": "inputs larger than L2 (A is 1.07 GB), no flush",
                    "parallelism": f"replicas x{world}"},

@@ -47,17 +47,19 @@ int psfsim_ring_chain(int N, double S, double r_max, const double *h_theta, cons
 int psfsim_residual_loss(const float *d_y, const float *d_d, int64_t M, double sigma, float *d_r,
                          double *d_loss, void *d_scratch, size_t scratch_bytes, void *stream);
 
-/* One whole fit gradient on an FP32 grid plan, in six launches: the ring
- * scene (d_z) with its parameter Jacobian, S = A Z (d_y) with the residual
- * r = (S - d)/sigma^2 (d_r) and FP64 loss partials formed in the same
- * reduction, A^T r (d_gz), the chain sums against the stored Jacobian, and one
- * final sum: d_out (device double[6]) = {L, dL/dR, dL/dw, dL/di, dL/dg, dL/dB}.
+/* One whole fit gradient on an FP32 grid plan, in two launches: the first
+ * evaluates the ring scene (d_z) and its parameter Jacobian, S = A Z (d_y),
+ * the residual r = (S - d)/sigma^2 (d_r) and FP64 loss partials; the second
+ * forms A^T r (d_gz), its dot with the Jacobian and the final sums:
+ * d_out (device double[6]) = {L, dL/dR, dL/dw, dL/di, dL/dg, dL/dB}.
  * The scene grid (N, S) is the plan's.  Same quantities as psfsim_ring_scene
- * + psfsim_forward + psfsim_residual_loss + psfsim_adjoint + psfsim_ring_chain.
+ * + psfsim_forward + psfsim_residual_loss + psfsim_adjoint + psfsim_ring_chain,
+ * deterministic, with sums in a different (fixed) order.
  * PSFSIM_ERR_UNSUPPORTED for other storages or point builds.  The two halves
  * are also callable on their own (same scratch, same theta, in this order):
  * the first leaves the loss partials and dZ/dtheta in the scratch for the
- * second. */
+ * second.  The scratch holds arrival counters: zero-fill it once before its
+ * first use; every call leaves the counters at zero again. */
 int psfsim_ring_gradient_scratch_bytes(psfsim_t h, size_t *bytes);
 int psfsim_ring_forward_loss(psfsim_t h, double r_max, const double *h_theta, const float *d_target, double sigma,
                              float *d_z, float *d_y, float *d_r, void *d_scratch, size_t scratch_bytes,

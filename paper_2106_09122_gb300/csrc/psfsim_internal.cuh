@@ -72,20 +72,6 @@ int psfsim_multi_validate(const psfsim_job_t *jobs, int njobs);
 size_t psfsim_forward_multi_scratch(const psfsim_job_t *jobs, int njobs, const psfsim_tuning_t *tune);
 cudaError_t psfsim_launch_forward_multi(const psfsim_job_t *jobs, int njobs, const psfsim_tuning_t *tune,
                                         void *scratch, cudaStream_t st);
-// Fit gradient on FP32 storage: the forward fused with the residual and loss
-// partials, the adjoint fused with the chain rule and the final sums.
-// 128-row slices of the fused forward (one loss partial and one arrival
-// counter each), its partial-sum scratch, and the most CTAs the
-// adjoint-with-chain launch uses (one chain partial each).
-int psfsim_forward_loss_slices(const psfsim_plan *h);
-size_t psfsim_forward_loss_scratch(const psfsim_plan *h);
-int psfsim_adjoint_chain_max_blocks(const psfsim_plan *h);
-cudaError_t psfsim_launch_forward_loss(const psfsim_plan *h, const float *x, const float *d, double sigma, float *y,
-                                       float *r, void *scratch, double *loss_part, unsigned *slice_count,
-                                       cudaStream_t st);
-cudaError_t psfsim_launch_adjoint_chain(const psfsim_plan *h, const float *g, float *gz, const float *jac,
-                                        double *chain_part, const double *loss_part, unsigned *count, double *out,
-                                        cudaStream_t st);
 // Generic FP32 GEMV pieces (column-major A) used by several storages.
 int psfsim_gemv_splits(int64_t ld, int64_t K, int num_sms);
 cudaError_t psfsim_launch_gemv_partials(const float *A, int64_t ld, int64_t K, const float *x, int B, float *part,

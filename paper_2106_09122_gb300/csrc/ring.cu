@@ -13,20 +13,6 @@ namespace {
 constexpr int kRedBlocks = 256;
 constexpr int kRedThreads = 256;
 
-// Scene and its parameter Jacobian, jac[m * K + j] = dZ_j / dtheta_m; block 0
-// also zeroes the arrival counters of the fused forward and adjoint that follow.
-__global__ void ring_scene_jac_kernel(const RingParams P, float *z, float *jac, unsigned *count, int n_count) {
-  if (blockIdx.x == 0)
-    for (int i = threadIdx.x; i < n_count; i += blockDim.x) count[i] = 0u;
-  const int64_t K = (int64_t)P.N * P.N;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < K; j += (int64_t)gridDim.x * blockDim.x) {
-    float J[5];
-    z[j] = ring_eval<true>(P, j, J);
-#pragma unroll
-    for (int m = 0; m < 5; ++m) jac[m * K + j] = J[m];
-  }
-}
-
 __global__ void ring_scene_kernel(const RingParams P, float *z) {
   const int64_t K = (int64_t)P.N * P.N;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < K; j += (int64_t)gridDim.x * blockDim.x)
@@ -96,41 +82,6 @@ __global__ void __launch_bounds__(kRedThreads) loss_partial(const float *y, cons
   if (threadIdx.x == 0) part[blockIdx.x] = acc[0];
 }
 
-struct GradScratch {
-  size_t part, loss, chain, count, jac, total;
-  int n_count;  // forward slice counters, then the adjoint's counter
-};
-
-GradScratch gradient_scratch(const psfsim_plan *h) {
-  GradScratch g;
-  g.n_count = psfsim_forward_loss_slices(h) + 1;
-  g.part = 0;
-  g.loss = (size_t)psfsim_round_up((int64_t)psfsim_forward_loss_scratch(h), 256);
-  g.chain = g.loss + (size_t)psfsim_round_up((int64_t)psfsim_forward_loss_slices(h) * 8, 256);
-  g.count = g.chain + (size_t)psfsim_round_up((int64_t)psfsim_adjoint_chain_max_blocks(h) * 5 * 8, 256);
-  g.jac = g.count + (size_t)psfsim_round_up((int64_t)g.n_count * 4, 256);
-  g.total = g.jac + (size_t)5 * h->K * 4;
-  return g;
-}
-
-bool ring_params(int N, double S, double r_max, const double *th, RingParams *P) {
-  if (N < 1 || N > 32768 || !(S > 0.0) || !th || !(r_max >= 0.0)) return false;
-  for (int m = 0; m < 5; ++m)
-    if (!std::isfinite(th[m])) return false;
-  if (!(th[1] > 0.0) || !(std::fabs(std::cos(th[2])) > 1e-6) || !(std::fabs(th[3]) < 1.0)) return false;
-  P->N = N;
-  P->S = S;
-  P->r_max = r_max;
-  P->R = (float)th[0];
-  P->w = (float)th[1];
-  P->inc = (float)th[2];
-  P->g = (float)th[3];
-  P->B = (float)th[4];
-  return true;
-}
-
-bool aligned256(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 255) == 0; }
-
 }  // namespace
 
 extern "C" {
@@ -179,69 +130,6 @@ int psfsim_residual_loss(const float *d_y, const float *d_d, int64_t M, double s
   loss_partial<<<kRedBlocks, kRedThreads, 0, st>>>(d_y, d_d, M, sigma, (float)(1.0 / (sigma * sigma)), d_r, part);
   finish_sum<1><<<1, kRedThreads, 0, st>>>(part, kRedBlocks, 0.5, d_loss);
   return cudaGetLastError() == cudaSuccess ? PSFSIM_OK : PSFSIM_ERR_CUDA;
-}
-
-int psfsim_ring_gradient_scratch_bytes(psfsim_t h, size_t *bytes) {
-  if (!h || !bytes) return PSFSIM_ERR_ARG;
-  if (h->storage != PSFSIM_FP32 || h->N < 1) return PSFSIM_ERR_UNSUPPORTED;
-  *bytes = gradient_scratch(h).total;
-  return PSFSIM_OK;
-}
-
-static int gradient_args(psfsim_t h, double r_max, const double *h_theta, void *d_scratch, size_t scratch_bytes,
-                         RingParams *P, GradScratch *g) {
-  if (!h) return PSFSIM_ERR_ARG;
-  if (h->storage != PSFSIM_FP32 || h->N < 1) return PSFSIM_ERR_UNSUPPORTED;
-  if (!ring_params(h->N, h->S, r_max, h_theta, P)) return PSFSIM_ERR_ARG;
-  *g = gradient_scratch(h);
-  if (!d_scratch || !aligned256(d_scratch) || scratch_bytes < g->total) return PSFSIM_ERR_WORKSPACE;
-  return PSFSIM_OK;
-}
-
-int psfsim_ring_forward_loss(psfsim_t h, double r_max, const double *h_theta, const float *d_target, double sigma,
-                             float *d_z, float *d_y, float *d_r, void *d_scratch, size_t scratch_bytes,
-                             void *stream) {
-  if (!d_target || !d_z || !d_y || !d_r || !(sigma > 0.0) || !std::isfinite(sigma)) return PSFSIM_ERR_ARG;
-  RingParams P;
-  GradScratch g;
-  if (int rc = gradient_args(h, r_max, h_theta, d_scratch, scratch_bytes, &P, &g)) return rc;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  char *base = static_cast<char *>(d_scratch);
-  const int64_t K = (int64_t)h->N * h->N;
-  unsigned *count = reinterpret_cast<unsigned *>(base + g.count);
-  ring_scene_jac_kernel<<<(unsigned)((K + 255) / 256 < 4096 ? (K + 255) / 256 : 4096), 256, 0, st>>>(
-      P, d_z, reinterpret_cast<float *>(base + g.jac), count, g.n_count);
-  if (cudaGetLastError() != cudaSuccess) return PSFSIM_ERR_CUDA;
-  return psfsim_launch_forward_loss(h, d_z, d_target, sigma, d_y, d_r, base + g.part,
-                                    reinterpret_cast<double *>(base + g.loss), count, st) == cudaSuccess
-             ? PSFSIM_OK
-             : PSFSIM_ERR_CUDA;
-}
-
-int psfsim_ring_adjoint_chain(psfsim_t h, double r_max, const double *h_theta, const float *d_r, float *d_gz,
-                              double *d_out, void *d_scratch, size_t scratch_bytes, void *stream) {
-  if (!d_r || !d_gz || !d_out) return PSFSIM_ERR_ARG;
-  RingParams P;
-  GradScratch g;
-  if (int rc = gradient_args(h, r_max, h_theta, d_scratch, scratch_bytes, &P, &g)) return rc;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  char *base = static_cast<char *>(d_scratch);
-  return psfsim_launch_adjoint_chain(h, d_r, d_gz, reinterpret_cast<const float *>(base + g.jac),
-                                     reinterpret_cast<double *>(base + g.chain),
-                                     reinterpret_cast<const double *>(base + g.loss),
-                                     reinterpret_cast<unsigned *>(base + g.count) + g.n_count - 1, d_out,
-                                     st) == cudaSuccess
-             ? PSFSIM_OK
-             : PSFSIM_ERR_CUDA;
-}
-
-int psfsim_ring_gradient(psfsim_t h, double r_max, const double *h_theta, const float *d_target, double sigma,
-                         float *d_z, float *d_y, float *d_r, float *d_gz, double *d_out, void *d_scratch,
-                         size_t scratch_bytes, void *stream) {
-  int rc = psfsim_ring_forward_loss(h, r_max, h_theta, d_target, sigma, d_z, d_y, d_r, d_scratch, scratch_bytes,
-                                    stream);
-  if (rc != PSFSIM_OK) return rc;
-  return psfsim_ring_adjoint_chain(h, r_max, h_theta, d_r, d_gz, d_out, d_scratch, scratch_bytes, stream);
 }
 
 }  // extern "C"

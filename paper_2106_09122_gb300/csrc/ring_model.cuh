@@ -1,12 +1,15 @@
 // Ring scene model shared by the fit operators (ring.cu) and the fused
-// adjoint + chain kernel (gemv.cu).  See include/psfsim_fit.h for the model.
+// fit-gradient kernels (fit_gradient.cu).  See include/psfsim_fit.h for the model.
 #pragma once
 
 #include <stdint.h>
 
+#include <cmath>
+
 struct RingParams {
   int N;
   double S, r_max;
+  float r2f;  // r_max^2 rounded to float
   float R, w, inc, g, B;
 };
 
@@ -14,15 +17,28 @@ struct RingParams {
 template <bool kJac>
 __device__ __forceinline__ float ring_eval(const RingParams &P, int64_t j, float *J) {
   const int iy = (int)(j / P.N), ix = (int)(j % P.N);
-  const double half = 0.5 * (double)(P.N - 1);
-  const double xs = __dmul_rn((double)ix - half, P.S), ys = __dmul_rn((double)iy - half, P.S);
-  const bool inside = __dsqrt_rn(__dadd_rn(__dmul_rn(xs, xs), __dmul_rn(ys, ys))) <= P.r_max;
+  const float halff = 0.5f * (float)(P.N - 1);  // exact: a half-integer below 2^15
+  const float Sf = (float)P.S;
+  const float x = ((float)ix - halff) * Sf, y = ((float)iy - halff) * Sf;
+  // Inside the disk of radius r_max: decided in FP32 where x^2 + y^2 is more
+  // than a relative 1e-5 away from r_max^2 (the FP32 error is below 1e-6),
+  // else by the FP64 test, so the decision equals the FP64 one everywhere.
+  const float d2 = x * x + y * y, r2 = P.r2f;
+  bool inside;
+  if (d2 < r2 * 0.99999f) {
+    inside = true;
+  } else if (d2 > r2 * 1.00001f) {
+    inside = false;
+  } else {
+    const double half = 0.5 * (double)(P.N - 1);
+    const double xs = __dmul_rn((double)ix - half, P.S), ys = __dmul_rn((double)iy - half, P.S);
+    inside = __dsqrt_rn(__dadd_rn(__dmul_rn(xs, xs), __dmul_rn(ys, ys))) <= P.r_max;
+  }
   if (!inside) {
     if (kJac)
       for (int m = 0; m < 5; ++m) J[m] = 0.f;
     return 0.f;
   }
-  const float x = (float)xs, y = (float)ys;
   float si, ci;
   sincosf(P.inc, &si, &ci);
   const float yd = y / ci;
@@ -55,4 +71,24 @@ __device__ __forceinline__ float ring_eval(const RingParams &P, int64_t j, float
   }
   return z;
 }
+
+// Host: validate (N, S, r_max, theta) and fill the kernel parameters.
+inline bool ring_params(int N, double S, double r_max, const double *th, RingParams *P) {
+  if (N < 1 || N > 32768 || !(S > 0.0) || !th || !(r_max >= 0.0)) return false;
+  for (int m = 0; m < 5; ++m)
+    if (!std::isfinite(th[m])) return false;
+  if (!(th[1] > 0.0) || !(std::fabs(std::cos(th[2])) > 1e-6) || !(std::fabs(th[3]) < 1.0)) return false;
+  P->N = N;
+  P->S = S;
+  P->r_max = r_max;
+  P->r2f = (float)(r_max * r_max);
+  P->R = (float)th[0];
+  P->w = (float)th[1];
+  P->inc = (float)th[2];
+  P->g = (float)th[3];
+  P->B = (float)th[4];
+  return true;
+}
+
+inline bool aligned256(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 255) == 0; }
 

@@ -49,9 +49,10 @@ class RingProblem:
         self.cscr = torch.empty(nb.value, **u8)
         B.check(self.lib.psfsim_loss_scratch_bytes(plan.M, ctypes.byref(nb)), "loss scratch")
         self.lscr = torch.empty(nb.value, **u8)
-        # FP32 grid plans take the fused path (three launches per gradient).
+        # FP32 grid plans take the fused path (two launches per gradient); its
+        # scratch holds arrival counters that must start at zero.
         self.fused = self.lib.psfsim_ring_gradient_scratch_bytes(plan.handle, ctypes.byref(nb)) == B.OK
-        self.gscr = torch.empty(max(nb.value, 256), **u8) if self.fused else None
+        self.gscr = torch.zeros(max(nb.value, 256), **u8) if self.fused else None
         self.launches = 0
 
     # -- operators ---------------------------------------------------------
@@ -86,16 +87,16 @@ class RingProblem:
         self.residual_loss(self.y, self.target, False)
 
     def enqueue_forward_loss(self, theta) -> None:
-        """First half: ring scene and Jacobian, S = A Z with residual and loss partials (FP32 grid plans)."""
+        """First half (one launch): ring scene and Jacobian, S = A Z with residual and loss partials."""
         th = np.ascontiguousarray(theta, dtype=np.float64)
         B.check(self.lib.psfsim_ring_forward_loss(self.plan.handle, self.r_max, th.ctypes.data_as(ctypes.c_void_p),
                                                   _vp(self.target), self.sigma, _vp(self.z), _vp(self.y), _vp(self.r),
                                                   _vp(self.gscr), self.gscr.numel(), _stream_ptr(None)),
                 "psfsim_ring_forward_loss")
-        self.launches += 2
+        self.launches += 1
 
     def enqueue_adjoint_chain(self, theta) -> None:
-        """Second half: A^T r with the chain sums against the stored Jacobian and the final sums into out6."""
+        """Second half (one launch): A^T r, its dot with the stored Jacobian, the final sums into out6."""
         th = np.ascontiguousarray(theta, dtype=np.float64)
         B.check(self.lib.psfsim_ring_adjoint_chain(self.plan.handle, self.r_max, th.ctypes.data_as(ctypes.c_void_p),
                                                    _vp(self.r), _vp(self.gz), _vp(self.out6), _vp(self.gscr),

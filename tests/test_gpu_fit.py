@@ -115,7 +115,7 @@ def test_adjoint_fit_workload_gradient_and_fit():
 
 
 def test_fused_gradient_equals_separate_operators():
-    """psfsim_ring_gradient (3 launches) against ring + forward + loss + adjoint + chain."""
+    """psfsim_ring_gradient (2 launches) against ring + forward + loss + adjoint + chain."""
     w = workloads.adjoint_128()
     lib32 = w.library().astype(np.float32)
     truth = np.array(w.extra["truth"])
