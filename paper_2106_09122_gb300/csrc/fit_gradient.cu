@@ -7,6 +7,11 @@
 //   adj_chain_kernel       A^T r, its dot with dZ/dtheta, and the final sums
 //                          {L, dL/dtheta}.
 //
+// Both kernels are launched with programmatic stream serialization: the
+// forward computes its scene values and streams A before it waits for the
+// kernel ahead of it (griddepcontrol.wait), so back-to-back gradients overlap
+// one adjoint's tail with the next forward's streaming.
+//
 // Split-K partial sums are combined inside the kernels: first across an
 // 8-CTA cluster through distributed shared memory, then by the last CTA to
 // arrive (an arrival counter per slice).  Every sum runs in an order fixed by
@@ -44,29 +49,30 @@ __global__ void __cluster_dims__(1, kFwdCluster, 1) __launch_bounds__(kFwdThread
   const int KS = gridDim.y, ks = blockIdx.y, G = KS / kFwdCluster, grp = ks / kFwdCluster;
   const int64_t j0 = K * ks / KS, j1 = K * (ks + 1) / KS;
   const int64_t tile0 = (int64_t)blockIdx.x * kRowsPerCta;
-  if (blockIdx.x == 0 && blockIdx.y == 0)  // the adjoint that follows starts from zeroed counters
-    for (int i = threadIdx.x; i < n_adj_count; i += kFwdThreads) adj_count[i] = 0u;
-  // Scene values of the column range; Z and dZ/dtheta of column j are stored
-  // by the CTA of tile j mod tiles, which spreads that work over the tiles.
-  for (int64_t j = j0 + threadIdx.x; j < j1; j += kFwdThreads) {
-    float v;
-    if (j % gridDim.x == blockIdx.x) {
-      float J[5];
-      v = ring_eval<true>(P, j, J);
-      z[j] = v;
-#pragma unroll
-      for (int m = 0; m < 5; ++m) jac[m * K + j] = J[m];
-    } else {
-      v = ring_eval<false>(P, j, nullptr);
-    }
-    xs[j - j0] = v;
-  }
+  ptx::griddep_launch_dependents();
+  // Until griddep_wait below, this kernel neither writes global memory nor
+  // reads anything an earlier kernel writes: it may overlap the tail of the
+  // kernel before it in the stream.
+  for (int64_t j = j0 + threadIdx.x; j < j1; j += kFwdThreads) xs[j - j0] = ring_eval<false>(P, j, nullptr);
   __syncthreads();
   {
     const int64_t r = tile0 + 4 * threadIdx.x;
     float acc[1][4] = {{0.f, 0.f, 0.f, 0.f}};
     if (r < ld) fwd_accumulate<1, true>(A, ld, K, xs, 0, r, j0, j1, acc);
     cpart[threadIdx.x] = make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
+  }
+  ptx::griddep_wait();
+  if (blockIdx.x == 0 && blockIdx.y == 0)  // the adjoint that follows starts from zeroed counters
+    for (int i = threadIdx.x; i < n_adj_count; i += kFwdThreads) adj_count[i] = 0u;
+  // Z and dZ/dtheta of column j are stored by the CTA of tile j mod tiles,
+  // which spreads that work over the tiles.
+  for (int64_t j = j0 + threadIdx.x; j < j1; j += kFwdThreads) {
+    if (j % gridDim.x == blockIdx.x) {
+      float J[5];
+      z[j] = ring_eval<true>(P, j, J);
+#pragma unroll
+      for (int m = 0; m < 5; ++m) jac[m * K + j] = J[m];
+    }
   }
   ptx::cluster_sync();
   const uint32_t q = ptx::cluster_ctarank();
@@ -142,6 +148,8 @@ __global__ void __launch_bounds__(kAdjThreads, 6)
                      float *__restrict__ gz, const ChainArgs c) {
   __shared__ float gzs[kStashCols];
   __shared__ float jacs[5][kStashCols];
+  ptx::griddep_launch_dependents();
+  ptx::griddep_wait();  // r and dZ/dtheta come from the forward kernel
   {
     const int64_t j0 = K * blockIdx.x / gridDim.x, j1 = K * (blockIdx.x + 1) / gridDim.x;
     for (int t = threadIdx.x; t < 5 * kStashCols; t += kAdjThreads) {
@@ -289,6 +297,22 @@ GradScratch gradient_scratch(const psfsim_plan *h) {
   return g;
 }
 
+// Launch configuration with programmatic stream serialization: the kernel may
+// be scheduled while the previous kernel in the stream finishes; it calls
+// griddep_wait before touching that kernel's results.
+cudaLaunchConfig_t pdl_config(dim3 grid, int threads, cudaStream_t st, cudaLaunchAttribute (&attr)[1]) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3((unsigned)threads, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
 int gradient_args(psfsim_t h, double r_max, const double *h_theta, void *d_scratch, size_t scratch_bytes,
                   RingParams *P, GradScratch *g) {
   if (!h) return PSFSIM_ERR_ARG;
@@ -320,12 +344,14 @@ int psfsim_ring_forward_loss(psfsim_t h, double r_max, const double *h_theta, co
   char *base = static_cast<char *>(d_scratch);
   unsigned *count = reinterpret_cast<unsigned *>(base + g.count);
   const float *A = reinterpret_cast<const float *>(h->ws + h->a_off);
-  const dim3 grid((unsigned)forward_tiles(h), (unsigned)forward_splits(h));
-  fwd_ring_loss_kernel<<<grid, kFwdThreads, 0, static_cast<cudaStream_t>(stream)>>>(
-      A, h->ld, h->M, h->K, P, d_z, reinterpret_cast<float *>(base + g.jac), reinterpret_cast<float *>(base + g.part),
-      d_target, sigma, (float)(1.0 / (sigma * sigma)), d_y, d_r, reinterpret_cast<double *>(base + g.loss), count,
-      count + g.n_slices, g.n_groups + 1);
-  return cudaGetLastError() == cudaSuccess ? PSFSIM_OK : PSFSIM_ERR_CUDA;
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg = pdl_config(dim3((unsigned)forward_tiles(h), (unsigned)forward_splits(h)),
+                                            kFwdThreads, static_cast<cudaStream_t>(stream), attr);
+  const cudaError_t e = cudaLaunchKernelEx(
+      &cfg, fwd_ring_loss_kernel, A, h->ld, h->M, h->K, P, d_z, reinterpret_cast<float *>(base + g.jac),
+      reinterpret_cast<float *>(base + g.part), d_target, sigma, (float)(1.0 / (sigma * sigma)), d_y, d_r,
+      reinterpret_cast<double *>(base + g.loss), count, count + g.n_slices, g.n_groups + 1);
+  return e == cudaSuccess ? PSFSIM_OK : PSFSIM_ERR_CUDA;
 }
 
 int psfsim_ring_adjoint_chain(psfsim_t h, double r_max, const double *h_theta, const float *d_r, float *d_gz,
@@ -344,13 +370,12 @@ int psfsim_ring_adjoint_chain(psfsim_t h, double r_max, const double *h_theta, c
                     g.n_slices,
                     reinterpret_cast<unsigned *>(base + g.count) + g.n_slices,
                     d_out};
-  const unsigned grid = (unsigned)adjoint_blocks(h, vec);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (vec)
-    adj_chain_kernel<true><<<grid, kAdjThreads, 0, st>>>(A, h->ld, h->M, h->K, d_r, d_gz, c);
-  else
-    adj_chain_kernel<false><<<grid, kAdjThreads, 0, st>>>(A, h->ld, h->M, h->K, d_r, d_gz, c);
-  return cudaGetLastError() == cudaSuccess ? PSFSIM_OK : PSFSIM_ERR_CUDA;
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg =
+      pdl_config(dim3((unsigned)adjoint_blocks(h, vec)), kAdjThreads, static_cast<cudaStream_t>(stream), attr);
+  const cudaError_t e = vec ? cudaLaunchKernelEx(&cfg, adj_chain_kernel<true>, A, h->ld, h->M, h->K, d_r, d_gz, c)
+                            : cudaLaunchKernelEx(&cfg, adj_chain_kernel<false>, A, h->ld, h->M, h->K, d_r, d_gz, c);
+  return e == cudaSuccess ? PSFSIM_OK : PSFSIM_ERR_CUDA;
 }
 
 int psfsim_ring_gradient(psfsim_t h, double r_max, const double *h_theta, const float *d_target, double sigma,

@@ -182,4 +182,13 @@ __device__ __forceinline__ float4 ld_dsmem_f4(const void *local, uint32_t rank) 
   return v;
 }
 
+// Programmatic dependent launch: let the next kernel in the stream (launched
+// with programmatic stream serialization) be scheduled early, and wait until
+// the kernels this one depends on have completed with their memory visible.
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 }  // namespace ptx
