@@ -204,6 +204,8 @@ def _gpu_arm(args, rank, world, local_rank):
     fwd_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
     adj_ms = float(np.mean([e[2].elapsed_time(e[3]) for e in ev]))
 
+    dev_out6 = prob.out6.cpu().numpy().copy()
+
     # e2e: a new observed image arrives from pinned host memory every step and
     # the loss + gradient come back to the host, through the same C-ABI calls
     hd = d.cpu().pin_memory()
@@ -227,6 +229,7 @@ def _gpu_arm(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
     e2e_ms = _allreduce_max(e2e_ms, dev)
+    e2e_out = hout.numpy().copy()
 
     # plain FP32 GEMV comparator (cuBLAS through torch) on the same stored A
     x = torch.from_numpy(x_np).to(dev)
@@ -298,7 +301,8 @@ def _gpu_arm(args, rank, world, local_rank):
                 "loss_last": float(hist[-1]), "theta": [float(v) for v in theta_fit],
                 "truth": [float(v) for v in truth]},
         "e2e": {"value": images / (e2e_ms / 1e3), "unit": "images/s",
-                "h2d_bytes_per_step": w.M * 4, "d2h_bytes_per_step": 6 * 8},
+                "h2d_bytes_per_step": w.M * 4, "d2h_bytes_per_step": 6 * 8,
+                "result_equals_device_path": bool(np.array_equal(e2e_out, dev_out6))},
         "gpu_launches": launches,
         "clocks": clk,
     }
@@ -710,6 +714,13 @@ def _profile_case(name: str) -> None:
         for _ in range(3):
             plan.forward(x)
             plan.adjoint(g)
+    elif name == "fit128":
+        from paper_2106_09122_gb300.fit import RingProblem
+        w = workloads.adjoint_128()
+        plan = Plan(torch.from_numpy(w.library().astype(np.float32)).to(dev), w.radii, w.s, N=w.N, S=w.S)
+        prob = RingProblem(plan, w.N, w.S, w.r_max, torch.rand(w.M, device=dev) * 1e-10, w.extra["sigma"])
+        for _ in range(3):
+            prob.enqueue_gradient(workloads.fit_init(w))
     else:
         raise SystemExit(f"unknown case {name}")
     torch.cuda.synchronize()
@@ -724,7 +735,8 @@ def main():
     ap.add_argument("--impl", default="psfsim", choices=["psfsim", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--main-only", action="store_true", help="skip the other workloads' measurements")
-    ap.add_argument("--case", default=None, help="run one small profiling case (fp32_128, tc128, fused512)")
+    ap.add_argument("--case", default=None,
+                    help="run one small profiling case (fp32_128, fit128, tc128, fused512)")
     args = ap.parse_args()
     if args.case:
         _profile_case(args.case)

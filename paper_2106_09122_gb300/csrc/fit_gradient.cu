@@ -12,8 +12,8 @@
 // kernel ahead of it (griddepcontrol.wait), so back-to-back gradients overlap
 // one adjoint's tail with the next forward's streaming.
 //
-// Split-K partial sums are combined inside the kernels: first across an
-// 8-CTA cluster through distributed shared memory, then by the last CTA to
+// Split-K partial sums are combined inside the kernels: first across a
+// 4-CTA cluster through distributed shared memory, then by the last CTA to
 // arrive (an arrival counter per slice).  Every sum runs in an order fixed by
 // the grid, never by arrival, so results are deterministic.  The counters
 // live in the caller's scratch, must be zero before the first call and are
@@ -28,16 +28,18 @@ using namespace psfsim_gemv;
 
 namespace {
 
-constexpr int kFwdCluster = 8;                        // CTAs (consecutive column chunks) per cluster
-constexpr int kSliceVec = kFwdThreads / kFwdCluster;  // row quads per 128-row slice
+constexpr int kFwdCluster = 4;                        // CTAs (consecutive column chunks) per cluster
+constexpr int kSliceVec = kFwdThreads / kFwdCluster;  // row quads per slice (64: 256 rows, two warps)
+static_assert(kSliceVec % 32 == 0 && kSliceVec <= kFwdThreads, "slices are whole warps");
 constexpr int kXCols = 2048;                          // most scene columns one CTA holds
 
 // CTA (tile, ks): rows [1024 tile, 1024 tile + 1024), columns
 // [K ks / KS, K (ks + 1) / KS) (at most kXCols).  Cluster rank q reduces
-// slice q (128 rows) of the tile over the cluster's 8 partials in rank order
-// and writes the group partial part[grp][rows]; the last of the G = KS / 8
-// groups to arrive for a slice adds the group partials in group order and
-// forms y, r and the slice's loss partial sum ((y - d)/sigma)^2.
+// slice q (256 rows) of the tile over the cluster's kFwdCluster partials in
+// rank order and writes the group partial part[grp][rows]; the last of the
+// G = KS / kFwdCluster groups to arrive for a slice adds the group partials
+// in group order and forms y, r and the slice's loss partial
+// sum ((y - d)/sigma)^2.
 __global__ void __cluster_dims__(1, kFwdCluster, 1) __launch_bounds__(kFwdThreads, 6)
     fwd_ring_loss_kernel(const float *__restrict__ A, int64_t ld, int64_t M, int64_t K, const RingParams P,
                          float *__restrict__ z, float *__restrict__ jac, float *__restrict__ part,
@@ -89,12 +91,15 @@ __global__ void __cluster_dims__(1, kFwdCluster, 1) __launch_bounds__(kFwdThread
   }
   ptx::cluster_sync();  // every rank has read the others' shared memory
   if (threadIdx.x >= kSliceVec) return;
+  // From here only the kSliceVec threads of the slice work (named barrier 1).
+  __shared__ unsigned last;
+  __shared__ double q2w[kSliceVec / 32];
   __threadfence();
-  __syncwarp();
+  ptx::named_barrier_sync(1, kSliceVec);
   const unsigned slot = blockIdx.x * kFwdCluster + q;
-  unsigned last = 0;
   if (threadIdx.x == 0) last = atomicAdd(slice_count + slot, 1u) == (unsigned)(G - 1);
-  if (!__shfl_sync(0xffffffffu, last, 0)) return;
+  ptx::named_barrier_sync(1, kSliceVec);
+  if (!last) return;
   __threadfence();
   double q2 = 0.0;
   if (rs < ld) {
@@ -118,8 +123,13 @@ __global__ void __cluster_dims__(1, kFwdCluster, 1) __launch_bounds__(kFwdThread
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) q2 += __shfl_xor_sync(0xffffffffu, q2, o);
+  if ((threadIdx.x & 31) == 0) q2w[threadIdx.x >> 5] = q2;
+  ptx::named_barrier_sync(1, kSliceVec);
   if (threadIdx.x == 0) {
-    loss_part[slot] = q2;
+    double t = q2w[0];
+#pragma unroll
+    for (int w = 1; w < kSliceVec / 32; ++w) t += q2w[w];
+    loss_part[slot] = t;
     slice_count[slot] = 0u;
   }
 }
@@ -236,8 +246,10 @@ int forward_tiles(const psfsim_plan *h) { return (int)((h->ld + kRowsPerCta - 1)
 
 // Column splits of the forward: a multiple of the cluster size; as many as
 // fit one wave of clusters, but never fewer than keep a CTA's columns within
-// kXCols, and (where possible) at least 8 columns per CTA.
-int forward_splits(const psfsim_plan *h) {
+// kXCols, and (where possible) at least 8 columns per CTA.  Fixed in the plan
+// at first use, so that the scratch size and every launch agree.
+int forward_splits(psfsim_plan *h) {
+  if (h->fit_ks > 0) return h->fit_ks;
   const int tiles = forward_tiles(h);
   int clusters = 0;
   cudaLaunchConfig_t cfg = {};
@@ -254,7 +266,8 @@ int forward_splits(const psfsim_plan *h) {
   const int64_t min_groups = (min_ks + kFwdCluster - 1) / kFwdCluster;
   if (groups < min_groups) groups = min_groups;
   if (groups < 1) groups = 1;
-  return (int)groups * kFwdCluster;
+  h->fit_ks = (int)groups * kFwdCluster;
+  return h->fit_ks;
 }
 
 int adjoint_blocks(const psfsim_plan *h, bool vec) {
@@ -281,7 +294,7 @@ struct GradScratch {
   int n_slices, n_groups, n_count;  // counters: slices, then groups + 1
 };
 
-GradScratch gradient_scratch(const psfsim_plan *h) {
+GradScratch gradient_scratch(psfsim_plan *h) {
   GradScratch g;
   g.n_slices = forward_tiles(h) * kFwdCluster;
   g.n_groups = (adjoint_max_blocks(h) + kChainGroup - 1) / kChainGroup;

@@ -40,6 +40,7 @@ struct psfsim_plan {
   size_t ws_bytes;
   int64_t a_off, lo_off, scale_off, geom_off, order_off, bstart_off, pts_off, status_off, libmax_off, plib_off;
   int device, num_sms;
+  int fit_ks;           // column splits of the fit-gradient forward, fixed at first use (0: not yet)
   CUtensorMap lib_map;  // 3D tensor map over the library for TMA staging
 };
 

@@ -182,6 +182,11 @@ __device__ __forceinline__ float4 ld_dsmem_f4(const void *local, uint32_t rank) 
   return v;
 }
 
+// Barrier `id` (1..15) over the first `count` threads of the CTA (whole warps).
+__device__ __forceinline__ void named_barrier_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 // Programmatic dependent launch: let the next kernel in the stream (launched
 // with programmatic stream serialization) be scheduled early, and wait until
 // the kernels this one depends on have completed with their memory visible.
