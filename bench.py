@@ -36,8 +36,8 @@ METRIC = "simulated images/s and GMAC/s (fraction of HBM/tensor roofline) vs pla
 # ncu capture of the current kernels (profiles/*.md).  The tensor-core figure is
 # from the 128^2 case and scales with the bytes of A (traffic / A = 1.0375 there).
 NCU_TRAFFIC = {
-    "forward": 1.073844e9 + 0.003246e9,        # fwd_partial_kernel, 128^2
-    "adjoint": 1.073871e9 + 0.002845e9,        # adj_kernel, 128^2
+    "forward": 1.073864e9 + 0.003710e9,        # fwd_ring_loss_kernel, 128^2
+    "adjoint": 1.074212e9 + 0.005124e9,        # adj_chain_kernel, 128^2
     "tc_gemm_per_A_byte": (1.086450e9 + 0.028076e9) / (16384 * 16384 * 4),
     "fused": 2.100080e9 + 0.128986e9,          # fused_kernel (quad-layout taps), 512^2, 32 scenes
 }
@@ -259,8 +259,8 @@ def _gpu_arm(args, rank, world, local_rank):
 
     hbm, _, peak_kind = _peaks()
     a_bytes = w.M * w.K * 4
-    fwd_bytes = a_bytes + w.K * 4 + w.M * 4
-    adj_bytes = a_bytes + w.M * 4 + w.K * 4
+    fwd_bytes = a_bytes + 3 * w.M * 4 + 6 * w.K * 4   # A, target; y, r; Z and dZ/dtheta
+    adj_bytes = a_bytes + w.M * 4 + 6 * w.K * 4       # A, r; gz, dZ/dtheta
     ms_per_step = elapsed_ms / nsteps
     images = world * nsteps
     dominant = "adjoint" if adj_ms > fwd_ms else "forward"

@@ -66,13 +66,20 @@ __global__ void __launch_bounds__(256) fwd_reduce_kernel(const float *__restrict
   }
 }
 
-int forward_splits(const psfsim_plan *h) {
-  const int64_t row_blocks = (h->ld + kRowsPerCta - 1) / kRowsPerCta;
-  int64_t ks = (int64_t)h->num_sms * 8 / row_blocks;
-  ks = ks < 1 ? 1 : ks;
-  const int64_t max_ks = h->K / 8 > 0 ? h->K / 8 : 1;
-  return (int)(ks < max_ks ? ks : max_ks);
+// Resident fwd_partial_kernel CTAs per SM (registers decide it), queried once.
+int fwd_ctas_per_sm() {
+  static const int per_sm = [] {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fwd_partial_kernel<1>, kFwdThreads, 0) != cudaSuccess) {
+      (void)cudaGetLastError();
+      n = 0;
+    }
+    return n > 0 ? n : 1;
+  }();
+  return per_sm;
 }
+
+int forward_splits(const psfsim_plan *h) { return psfsim_gemv_splits(h->ld, h->K, h->num_sms); }
 
 // gx[b, j] = sum_i A[i, j] g[b, i]; CTA c owns the contiguous column range
 // [K c / G, K (c+1) / G).
@@ -123,9 +130,11 @@ cudaError_t psfsim_launch_gemv_partials(const float *A, int64_t ld, int64_t K, c
   return cudaSuccess;
 }
 
+// Column splits: one wave of resident CTAs over the row tiles (at least 8
+// columns per split).
 int psfsim_gemv_splits(int64_t ld, int64_t K, int num_sms) {
   const int64_t row_blocks = (ld + kRowsPerCta - 1) / kRowsPerCta;
-  int64_t ks = (int64_t)num_sms * 8 / row_blocks;
+  int64_t ks = (int64_t)num_sms * fwd_ctas_per_sm() / row_blocks;
   ks = ks < 1 ? 1 : ks;
   const int64_t max_ks = K / 8 > 0 ? K / 8 : 1;
   return (int)(ks < max_ks ? ks : max_ks);
