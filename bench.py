@@ -385,6 +385,51 @@ def _path_batched(dev, stream, hbm, with_oracle):
     return out
 
 
+def _path_bf16(dev, stream, hbm, with_oracle):
+    """The batched 256^2 workload with plain BF16 storage (hi alone: 8 x 8.6 GB), one multi-job
+    tcgen05 launch: half the bytes of split-BF16 at 2^-8 instead of 2^-17 storage error."""
+    import torch
+    from paper_2106_09122_gb300 import Plan
+    from paper_2106_09122_gb300.serve import MultiForward
+    from synth import workloads
+    w = workloads.batched_256()
+    nl, B = len(w.lam_ratios), w.extra["scenes"]
+    libs = [w.library(l).astype(np.float32) for l in range(nl)]
+    plans = [Plan(torch.from_numpy(lb).to(dev), w.radii, w.s, N=w.N, S=w.S, storage="bf16") for lb in libs]
+    mf = MultiForward(plans, [B] * nl)
+    X_np = []
+    for l in range(nl):
+        xs = np.empty((B, w.K), dtype=np.float32)
+        for b in range(B):
+            xs[b] = workloads.random_ring_scene(w.N, w.S, w.r_max, w.seed + 100000 * (l + 1) + b).ravel()
+        X_np.append(xs)
+        mf.x[l].copy_(torch.from_numpy(xs))
+    mf.count.fill_(B)
+    ms = _timed(mf.enqueue, 10, stream)
+    a_bytes = nl * (2 * w.M * w.K + B * w.K * 4 + B * w.M * 4)
+    out = {"workload": "batched_bf16_256: the batched 256^2 workload (8 wavelengths x 64 scenes) with BF16 "
+                       "storage, 8 x A 65536^2 (69 GB) in one launch",
+           "images_per_s": nl * B / (ms / 1e3), "ms_per_batch": ms,
+           "gmac_per_s": nl * B * w.M * w.K / (ms / 1e3) / 1e9,
+           "roofline": {"bound": "hbm", "achieved": a_bytes / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                        "frac": a_bytes / (ms / 1e3) / 1e9 / hbm,
+                        "kernel": "tc_gemm_kernel, 8 jobs, one MMA (N = 2 x 64) per k-step (+ split, reduce)",
+                        "intensity_note": "2 x 128 flop per 2-byte element = 128 flop/byte < bf16 ridge ~278"},
+           "tolerance": 2.0 ** -8 + 2.5e-5,
+           "status": plans[0].sync_status()}
+    if with_oracle:
+        per = []
+        for l in range(nl):
+            rows = np.sort(np.random.default_rng(91 + l).choice(w.M, 12, replace=False))
+            Yr = mf.y[l][:4, torch.from_numpy(rows).to(dev)].cpu().numpy()
+            per.append(_rows_error(libs[l], w.radii, w.N, w.S, X_np[l][:4], Yr, rows)["max_bound_rel_error"])
+        out["error_vs_oracle_per_wavelength"] = {"max_bound_rel_error": per, "rows_per_wavelength": 12,
+                                                 "scenes_per_wavelength": 4}
+    del plans, mf
+    torch.cuda.empty_cache()
+    return out
+
+
 def _path_fused(dev, stream, with_oracle):
     """Fused 512^2 workload: A (275 GB in FP32) regenerated on chip for 32 scenes."""
     import torch
@@ -696,10 +741,10 @@ def _profile_case(name: str) -> None:
         X = torch.from_numpy(workloads.scene_batch(w, 32, kind="two_ring").astype(np.float32)).to(dev)
         for _ in range(2):
             plan.forward(X)
-    elif name == "tc128":
+    elif name in ("tc128", "bf16_128"):
         w = workloads.adjoint_128()
         plan = Plan(torch.from_numpy(w.library().astype(np.float32)).to(dev), w.radii, w.s, N=w.N, S=w.S,
-                    storage="split_bf16")
+                    storage="split_bf16" if name == "tc128" else "bf16")
         X = torch.rand(64, w.K, device=dev)
         for _ in range(3):
             plan.forward(X)
@@ -736,7 +781,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--main-only", action="store_true", help="skip the other workloads' measurements")
     ap.add_argument("--case", default=None,
-                    help="run one small profiling case (fp32_128, fit128, tc128, fused512)")
+                    help="run one small profiling case (fp32_128, fit128, tc128, bf16_128, fused512)")
     args = ap.parse_args()
     if args.case:
         _profile_case(args.case)
@@ -764,6 +809,7 @@ def main():
         oracle_ok = rank == 0 and world == 1 and not args.no_cpu_baseline
         out["other_workloads"] = {
             "batched_split_bf16_256_8_wavelengths": _path_batched(dev, stream, hbm, oracle_ok),
+            "batched_bf16_256_8_wavelengths": _path_bf16(dev, stream, hbm, oracle_ok),
             "fused_512": _path_fused(dev, stream, oracle_ok),
             "uneven_500": _path_uneven(dev, stream, hbm, oracle_ok),
             "nearest_vs_linear_128": _path_nearest(dev),

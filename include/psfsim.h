@@ -54,13 +54,22 @@ enum psfsim_status {
 /* Storage of A.  FP32: column-major float32 (each PSF contiguous, as the
  * paper saves one flattened PSF per iteration, Sec. 2).  SPLIT_BF16: row-major
  * bf16 hi + lo with a power-of-two float32 scale per column, for the
- * tensor-core path.  FP32_SYM: FP32 columns of the x > 0, y > 0 quadrant only,
+ * tensor-core path.  BF16: the hi part alone (row-major bf16 with the same
+ * per-column scale): half the bytes, each element rounded to 8 significant
+ * bits, so results carry up to 2^-8 of the error bound (tensor-core forward,
+ * CUDA-core adjoint).  FP32_SYM: FP32 columns of the x > 0, y > 0 quadrant only,
  * inside the last radius: the other three quadrants' columns are exact
  * quarter turns of these and the rest are zero (even N, grid builds only;
  * same results as FP32 up to the order of the sums).  FUSED: A is never
  * stored; tiles are regenerated from the library on every product (the
  * paper's "standard interpolation method", Table 4, done on chip). */
-enum psfsim_storage { PSFSIM_FP32 = 0, PSFSIM_SPLIT_BF16 = 1, PSFSIM_FP32_SYM = 2, PSFSIM_FUSED = 3 };
+enum psfsim_storage {
+  PSFSIM_FP32 = 0,
+  PSFSIM_SPLIT_BF16 = 1,
+  PSFSIM_BF16 = 2,
+  PSFSIM_FUSED = 3,
+  PSFSIM_FP32_SYM = 4
+};
 
 /* Radial interpolation (Sec. 2 compares linear and nearest). */
 enum psfsim_interp { PSFSIM_LINEAR = 0, PSFSIM_NEAREST = 1 };
@@ -69,10 +78,10 @@ enum psfsim_interp { PSFSIM_LINEAR = 0, PSFSIM_NEAREST = 1 };
 typedef struct {
   int32_t storage, interp, n, n_r;
   int64_t M, K;
-  int64_t ld;           /* FP32: column stride in floats; SPLIT_BF16: row stride in elements */
-  int64_t a_offset;     /* FP32: A; SPLIT_BF16: hi */
+  int64_t ld;           /* FP32: column stride in floats; SPLIT_BF16, BF16: row stride in elements */
+  int64_t a_offset;     /* FP32: A; SPLIT_BF16, BF16: hi */
   int64_t lo_offset;    /* SPLIT_BF16: lo (else -1) */
-  int64_t scale_offset; /* SPLIT_BF16: float32 per-column scale (else -1) */
+  int64_t scale_offset; /* SPLIT_BF16, BF16: float32 per-column scale (else -1) */
   int64_t workspace_bytes;
   int64_t K_stored;     /* columns held (K; FP32_SYM / FUSED: quadrant columns inside the last radius) */
 } psfsim_info_t;

@@ -21,8 +21,8 @@ int check_radii(const double *r, int n_r) {
 }
 
 bool storage_ok(int storage) {
-  return storage == PSFSIM_FP32 || storage == PSFSIM_SPLIT_BF16 || storage == PSFSIM_FP32_SYM ||
-         storage == PSFSIM_FUSED;
+  return storage == PSFSIM_FP32 || storage == PSFSIM_SPLIT_BF16 || storage == PSFSIM_BF16 ||
+         storage == PSFSIM_FP32_SYM || storage == PSFSIM_FUSED;
 }
 
 int common_build(const float *d_lib, const double *h_radii, int n_r, int n, double s, int N, double S,
@@ -164,7 +164,7 @@ int psfsim_forward_scratch_bytes(psfsim_t h, int B, size_t *bytes) {
     *bytes = psfsim_forward_fp32_scratch(h, B);
     return PSFSIM_OK;
   }
-  if (h->storage == PSFSIM_SPLIT_BF16) {
+  if (h->storage == PSFSIM_SPLIT_BF16 || h->storage == PSFSIM_BF16) {
     *bytes = psfsim_forward_tc_scratch(h, B);
     return PSFSIM_OK;
   }
@@ -185,7 +185,7 @@ int psfsim_adjoint_scratch_bytes(psfsim_t h, int B, size_t *bytes) {
     *bytes = 0;
     return PSFSIM_OK;
   }
-  if (h->storage == PSFSIM_SPLIT_BF16) {
+  if (h->storage == PSFSIM_SPLIT_BF16 || h->storage == PSFSIM_BF16) {
     *bytes = psfsim_adjoint_split_scratch(h, B);
     return PSFSIM_OK;
   }
@@ -206,7 +206,7 @@ int psfsim_forward(psfsim_t h, const float *d_x, int B, float *d_y, void *d_scra
     return psfsim_launch_forward_fp32(h, d_x, B, d_y, d_scratch, st) == cudaSuccess ? PSFSIM_OK
                                                                                     : PSFSIM_ERR_CUDA;
   }
-  if (h->storage == PSFSIM_SPLIT_BF16) {
+  if (h->storage == PSFSIM_SPLIT_BF16 || h->storage == PSFSIM_BF16) {
     const size_t need = psfsim_forward_tc_scratch(h, B);
     if (!d_scratch || !aligned(d_scratch, 256) || scratch_bytes < need) return PSFSIM_ERR_WORKSPACE;
     return psfsim_launch_forward_tc(h, d_x, B, d_y, d_scratch, st) == cudaSuccess ? PSFSIM_OK : PSFSIM_ERR_CUDA;
@@ -231,7 +231,7 @@ int psfsim_adjoint(psfsim_t h, const float *d_g, int B, float *d_gx, void *d_scr
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (h->storage == PSFSIM_FP32)
     return psfsim_launch_adjoint_fp32(h, d_g, B, d_gx, st) == cudaSuccess ? PSFSIM_OK : PSFSIM_ERR_CUDA;
-  if (h->storage == PSFSIM_SPLIT_BF16) {
+  if (h->storage == PSFSIM_SPLIT_BF16 || h->storage == PSFSIM_BF16) {
     const size_t need = psfsim_adjoint_split_scratch(h, B);
     if (!d_scratch || !aligned(d_scratch, 256) || scratch_bytes < need) return PSFSIM_ERR_WORKSPACE;
     return psfsim_launch_adjoint_split(h, d_g, B, d_gx, d_scratch, st) == cudaSuccess ? PSFSIM_OK

@@ -1,13 +1,13 @@
-// Split-BF16 storage of A for the tensor-core path.
+// Split-BF16 and BF16 storage of A for the tensor-core path.
 //
 // A_ij (the same lerp + bilinear-rotation element as the FP32 build, Sec. 2)
 // is stored as sigma_j (hi_ij + lo_ij): sigma_j is the smallest power of two
 // >= max(max|L_k|, max|L_{k+1}|) over the column's radial bracket (an exact
 // bound on |A_ij|, since the lerp and bilinear weights are convex), hi =
-// RN_bf16(A_ij / sigma_j), lo = RN_bf16(A_ij / sigma_j - hi).  hi and lo are
-// row-major [rows][ld] (each image pixel's row contiguous along the scene
-// pixels: K-major for the MMA), ld = K rounded up to 64, rows = M rounded up
-// to 128; padding is zero.
+// RN_bf16(A_ij / sigma_j), lo = RN_bf16(A_ij / sigma_j - hi); BF16 storage
+// keeps hi alone.  hi and lo are row-major [rows][ld] (each image pixel's row
+// contiguous along the scene pixels: K-major for the MMA), ld = K rounded up
+// to 64, rows = M rounded up to 128; padding is zero.
 #include <cuda_bf16.h>
 
 #include "psfsim_internal.cuh"
@@ -46,7 +46,7 @@ struct SplitParams {
   const float *lib;
   const float *libmax;
   __nv_bfloat16 *hi;
-  __nv_bfloat16 *lo;
+  __nv_bfloat16 *lo;  // null for BF16 storage
   float *scale;
 };
 
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(256) split_build_kernel(const SplitParams P) {
       const int row = c >> 3, part = c & 7;
       const int64_t off = (mt * kTileRows + row) * P.ld + kt * kTileCols + part * 8;
       *reinterpret_cast<uint4 *>(P.hi + off) = *reinterpret_cast<const uint4 *>(&thi[row][part * 8]);
-      *reinterpret_cast<uint4 *>(P.lo + off) = *reinterpret_cast<const uint4 *>(&tlo[row][part * 8]);
+      if (P.lo) *reinterpret_cast<uint4 *>(P.lo + off) = *reinterpret_cast<const uint4 *>(&tlo[row][part * 8]);
     }
     __syncthreads();
   }
@@ -144,7 +144,7 @@ cudaError_t psfsim_launch_split_build(psfsim_plan *h, cudaStream_t st) {
   P.lib = h->d_lib;
   P.libmax = libmax;
   P.hi = reinterpret_cast<__nv_bfloat16 *>(h->ws + h->a_off);
-  P.lo = reinterpret_cast<__nv_bfloat16 *>(h->ws + h->lo_off);
+  P.lo = h->lo_off >= 0 ? reinterpret_cast<__nv_bfloat16 *>(h->ws + h->lo_off) : nullptr;
   P.scale = reinterpret_cast<float *>(h->ws + h->scale_off);
   int per_sm = 1;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_build_kernel, 256, 0)) != cudaSuccess)

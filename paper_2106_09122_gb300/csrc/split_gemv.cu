@@ -1,8 +1,8 @@
-// Adjoint A^T g for split-BF16 storage (row-major hi/lo, per-column scale):
-// gx[b, j] = sigma_j sum_i (hi_ij + lo_ij) g[b, i].  Each thread owns 8
-// consecutive columns (one 16-byte load of hi and of lo per row); the rows
-// are split KS ways into partial sums in caller scratch, reduced in a fixed
-// order afterwards (deterministic).
+// Adjoint A^T g for split-BF16 and BF16 storage (row-major hi[/lo],
+// per-column scale): gx[b, j] = sigma_j sum_i (hi_ij + lo_ij) g[b, i] (lo = 0
+// for BF16).  Each thread owns 8 consecutive columns (one 16-byte load of hi,
+// and of lo, per row); the rows are split KS ways into partial sums in caller
+// scratch, reduced in a fixed order afterwards (deterministic).
 #include <cuda_bf16.h>
 
 #include "psfsim_internal.cuh"
@@ -20,6 +20,15 @@ __device__ __forceinline__ uint4 ld_stream16(const void *p) {
   return v;
 }
 
+__device__ __forceinline__ void unpack8(uint4 h, float (&a)[8]) {
+  const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    a[2 * t] = __uint_as_float(hw[t] << 16);
+    a[2 * t + 1] = __uint_as_float(hw[t] & 0xFFFF0000u);
+  }
+}
+
 __device__ __forceinline__ void unpack8(uint4 h, uint4 l, float (&a)[8]) {
   const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
 #pragma unroll
@@ -29,7 +38,16 @@ __device__ __forceinline__ void unpack8(uint4 h, uint4 l, float (&a)[8]) {
   }
 }
 
-template <int BB>
+// Row i's 8 columns from j: hi + lo (kLo) or hi alone.
+template <bool kLo>
+__device__ __forceinline__ void load8(const __nv_bfloat16 *hi, const __nv_bfloat16 *lo, int64_t off, float (&a)[8]) {
+  if (kLo)
+    unpack8(ld_stream16(hi + off), ld_stream16(lo + off), a);
+  else
+    unpack8(ld_stream16(hi + off), a);
+}
+
+template <int BB, bool kLo>
 __global__ void __launch_bounds__(kThreads) adj_split_partial(const __nv_bfloat16 *__restrict__ hi,
                                                               const __nv_bfloat16 *__restrict__ lo,
                                                               const float *__restrict__ scale, int64_t ld,
@@ -47,11 +65,9 @@ __global__ void __launch_bounds__(kThreads) adj_split_partial(const __nv_bfloat1
   const float *gb = g + (int64_t)b0 * M;
   int64_t i = i0;
   for (; i + 2 <= i1; i += 2) {
-    const uint4 h0 = ld_stream16(hi + i * ld + j), l0 = ld_stream16(lo + i * ld + j);
-    const uint4 h1 = ld_stream16(hi + (i + 1) * ld + j), l1 = ld_stream16(lo + (i + 1) * ld + j);
     float a0[8], a1[8];
-    unpack8(h0, l0, a0);
-    unpack8(h1, l1, a1);
+    load8<kLo>(hi, lo, i * ld + j, a0);
+    load8<kLo>(hi, lo, (i + 1) * ld + j, a1);
 #pragma unroll
     for (int b = 0; b < BB; ++b) {
       const float g0 = __ldg(gb + (int64_t)b * M + i), g1 = __ldg(gb + (int64_t)b * M + i + 1);
@@ -61,7 +77,7 @@ __global__ void __launch_bounds__(kThreads) adj_split_partial(const __nv_bfloat1
   }
   for (; i < i1; ++i) {
     float a0[8];
-    unpack8(ld_stream16(hi + i * ld + j), ld_stream16(lo + i * ld + j), a0);
+    load8<kLo>(hi, lo, i * ld + j, a0);
 #pragma unroll
     for (int b = 0; b < BB; ++b) {
       const float g0 = __ldg(gb + (int64_t)b * M + i);
@@ -93,10 +109,13 @@ int adjoint_splits(const psfsim_plan *h) {
 template <int BB>
 cudaError_t group(const psfsim_plan *h, const float *g, int B, int b0, float *part, int KS, cudaStream_t st) {
   const __nv_bfloat16 *hi = reinterpret_cast<const __nv_bfloat16 *>(h->ws + h->a_off);
-  const __nv_bfloat16 *lo = reinterpret_cast<const __nv_bfloat16 *>(h->ws + h->lo_off);
   const float *scale = reinterpret_cast<const float *>(h->ws + h->scale_off);
   dim3 grid((unsigned)((h->ld + kColsPerCta - 1) / kColsPerCta), (unsigned)KS);
-  adj_split_partial<BB><<<grid, kThreads, 0, st>>>(hi, lo, scale, h->ld, h->M, g, B, b0, part);
+  if (h->lo_off >= 0)
+    adj_split_partial<BB, true><<<grid, kThreads, 0, st>>>(
+        hi, reinterpret_cast<const __nv_bfloat16 *>(h->ws + h->lo_off), scale, h->ld, h->M, g, B, b0, part);
+  else
+    adj_split_partial<BB, false><<<grid, kThreads, 0, st>>>(hi, nullptr, scale, h->ld, h->M, g, B, b0, part);
   return cudaGetLastError();
 }
 

@@ -1,4 +1,5 @@
-// Batched S = A Z (Eq. 6) on the 5th-generation tensor cores for split-BF16 A.
+// Batched S = A Z (Eq. 6) on the 5th-generation tensor cores for split-BF16
+// (and BF16) A.
 //
 // Y[b, i] = sum_j sigma_j (hi_ij + lo_ij) x_bj.  The scene batch is scaled by
 // sigma_j and split exactly into three bf16 parts x' = x1 + x2 + x3 (24 bits),
@@ -7,6 +8,9 @@
 // and the epilogue sums the three column blocks: (hi + lo)(x1 + x2) + hi x3,
 // i.e. only the lo * x3 term (< 2^-24 relative) is dropped; what remains is
 // the 2^-17 relative storage error of hi + lo and the FP32 accumulation.
+// BF16 storage has no lo: one MMA per k-step over two x parts,
+// D[:, 0:2Bp] += hi * [x1 x2]^T, so the result carries the 2^-8 relative
+// storage error of hi and the dropped hi * x3 term (< 2^-16 relative).
 //
 // Persistent warp-specialised kernel, one CTA per SM:
 //   warp 0  TMA producer (2D tiled loads, 128-byte swizzle) into a smem ring
@@ -41,6 +45,8 @@ constexpr int kMaxChunk = 8;     // <= 64 accumulating MMAs between drains
 struct TcJob {
   int64_t rows, M;
   int Bp, KS, m_tiles, k_tiles;
+  int has_lo;          // split-BF16 (hi + lo) or BF16 (hi alone)
+  int xparts;          // bf16 parts of x in the B operand: 3 (split-BF16) or 2 (BF16)
   int unit_begin;      // first work unit of this job
   int cap;             // scenes in the job's buffers (<= Bp)
   const int *count;    // device int: scenes present (NULL: all cap)
@@ -53,6 +59,7 @@ struct TcMulti {
   TcJob job[kMaxJobs];
   int njobs, units, stages, chunk;
   uint32_t stage_bytes;
+  uint32_t x_off;  // byte offset of the x tile in a stage: after hi and lo, or after hi alone
   int *status;
 };
 
@@ -125,7 +132,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       const TcJob &J = P.job[jb];
       const int lu = u - J.unit_begin;
       const int ks = lu / J.m_tiles, mt = lu % J.m_tiles;
-      const uint32_t tx = 2 * kTileBytes + (uint32_t)(3 * J.Bp) * BK * 2;
+      const uint32_t tx = (J.has_lo ? 2 : 1) * kTileBytes + (uint32_t)(J.xparts * J.Bp) * BK * 2;
       for (int kt = k_begin(J, ks); kt < k_begin(J, ks + 1); ++kt, ++it) {
         const int s = (int)(it % P.stages);
         if (!ptx::mbar_wait_bounded(&empty_bar[s], ((it / P.stages) & 1) ^ 1)) {
@@ -136,8 +143,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         uint8_t *st = smem + (size_t)s * P.stage_bytes;
         ptx::mbar_arrive_expect_tx(&full_bar[s], tx);
         ptx::tma_load_2d(st, &P.map[jb][0], kt * BK, mt * BM, &full_bar[s]);
-        ptx::tma_load_2d(st + kTileBytes, &P.map[jb][1], kt * BK, mt * BM, &full_bar[s]);
-        ptx::tma_load_2d(st + 2 * kTileBytes, &P.map[jb][2], kt * BK, 0, &full_bar[s]);
+        if (J.has_lo) ptx::tma_load_2d(st + kTileBytes, &P.map[jb][1], kt * BK, mt * BM, &full_bar[s]);
+        ptx::tma_load_2d(st + P.x_off, &P.map[jb][2], kt * BK, 0, &full_bar[s]);
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -148,8 +155,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       const TcJob &J = P.job[find_job(P, u)];
       const int ks = (u - J.unit_begin) / J.m_tiles;
       const int k0 = k_begin(J, ks), k1 = k_begin(J, ks + 1);
-      const uint32_t idesc3 = ptx::idesc_bf16_f32(BM, 3 * J.Bp);
+      const uint32_t idesc3 = ptx::idesc_bf16_f32(BM, J.xparts * J.Bp);
       const uint32_t idesc2 = ptx::idesc_bf16_f32(BM, 2 * J.Bp);
+      const bool has_lo = J.has_lo != 0;
       for (int kc = k0; kc < k1 && ok; kc += P.chunk, ++c) {
         const int kc1 = min(kc + P.chunk, k1);
         const uint32_t acc = c & 1;
@@ -171,12 +179,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           const uint8_t *st = smem + (size_t)s * P.stage_bytes;
           const uint64_t dh = ptx::smem_desc_sw128(st);
           const uint64_t dl = ptx::smem_desc_sw128(st + kTileBytes);
-          const uint64_t dx = ptx::smem_desc_sw128(st + 2 * kTileBytes);
+          const uint64_t dx = ptx::smem_desc_sw128(st + P.x_off);
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             const uint64_t adv = (uint64_t)(kk * 32) >> 4;  // 16 bf16 = 32 bytes along K
             ptx::mma_bf16(d_tmem, dh + adv, dx + adv, idesc3, (kt > kc || kk > 0) ? 1u : 0u);
-            ptx::mma_bf16(d_tmem, dl + adv, dx + adv, idesc2, 1u);
+            if (has_lo) ptx::mma_bf16(d_tmem, dl + adv, dx + adv, idesc2, 1u);
           }
           ptx::mma_commit(&empty_bar[s]);
         }
@@ -199,6 +207,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       const int ks = lu / J.m_tiles, mt = lu % J.m_tiles;
       const int k0 = k_begin(J, ks), k1 = k_begin(J, ks + 1);
       const int Bp = J.Bp;
+      const bool third = J.xparts == 3;
       float sum[kMaxBp];
 #pragma unroll
       for (int t = 0; t < kMaxBp; ++t) sum[t] = 0.f;
@@ -226,10 +235,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             float v0[16], v1[16], v2[16];
             ptx::tmem_ld16(tacc + q * 16, v0);
             ptx::tmem_ld16(tacc + Bp + q * 16, v1);
-            ptx::tmem_ld16(tacc + 2 * Bp + q * 16, v2);
+            if (third) ptx::tmem_ld16(tacc + 2 * Bp + q * 16, v2);
             ptx::tmem_ld_wait();
+            if (third) {
 #pragma unroll
-            for (int t = 0; t < 16; ++t) sum[q * 16 + t] += (v0[t] + v1[t]) + v2[t];
+              for (int t = 0; t < 16; ++t) sum[q * 16 + t] += (v0[t] + v1[t]) + v2[t];
+            } else {
+#pragma unroll
+              for (int t = 0; t < 16; ++t) sum[q * 16 + t] += v0[t] + v1[t];
+            }
           }
         }
         ptx::tc_fence_before();
@@ -314,7 +328,7 @@ struct JobPlan {
 struct MultiPlan {
   JobPlan jp[kMaxJobs];
   int njobs, units, stages, chunk;
-  uint32_t stage_bytes;
+  uint32_t stage_bytes, x_off;
   size_t smem, scratch;
 };
 
@@ -363,7 +377,18 @@ MultiPlan plan_multi(const JobSpec *jobs, int nj, const psfsim_tuning_t *tune) {
   }
   mp.units = units;
   mp.scratch = off;
-  mp.stage_bytes = (uint32_t)psfsim_round_up(2 * kTileBytes + 3 * Bp_max * BK * 2, 1024);
+  // A stage holds hi, lo (when any job has one) and the x tile; without lo
+  // the stage is smaller, so more stages (bytes in flight) fit.
+  bool any_lo = false;
+  int x_rows = 0;  // largest B operand: x parts x Bp
+  for (int j = 0; j < nj; ++j) {
+    const bool lo = jobs[j].h->lo_off >= 0;
+    any_lo = any_lo || lo;
+    const int r = (lo ? 3 : 2) * mp.jp[j].Bp;
+    x_rows = r > x_rows ? r : x_rows;
+  }
+  mp.x_off = (any_lo ? 2 : 1) * kTileBytes;
+  mp.stage_bytes = (uint32_t)psfsim_round_up(mp.x_off + (int64_t)x_rows * BK * 2, 1024);
   int fit = (int)((220 * 1024) / mp.stage_bytes);
   fit = fit > kMaxStages ? kMaxStages : fit;
   mp.stages = tune && tune->stages >= 2 && tune->stages < fit ? tune->stages : fit;
@@ -385,11 +410,15 @@ cudaError_t launch_multi(const JobSpec *jobs, int nj, const MultiPlan &mp, void 
     xsplit_kernel<<<h->num_sms * 4, 256, 0, st>>>(jobs[j].x, jobs[j].cap, jobs[j].count, p.Bp, h->K, h->ld, scale,
                                                   xs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const bool has_lo = h->lo_off >= 0;
     if (!encode_bf16_2d(&P.map[j][0], h->ws + h->a_off, (uint64_t)h->ld, (uint64_t)p.rows, BK, BM) ||
-        !encode_bf16_2d(&P.map[j][1], h->ws + h->lo_off, (uint64_t)h->ld, (uint64_t)p.rows, BK, BM) ||
-        !encode_bf16_2d(&P.map[j][2], xs, (uint64_t)h->ld, (uint64_t)(3 * p.Bp), BK, (uint32_t)(3 * p.Bp)))
+        (has_lo && !encode_bf16_2d(&P.map[j][1], h->ws + h->lo_off, (uint64_t)h->ld, (uint64_t)p.rows, BK, BM)) ||
+        !encode_bf16_2d(&P.map[j][2], xs, (uint64_t)h->ld, (uint64_t)(3 * p.Bp), BK,
+                        (uint32_t)((has_lo ? 3 : 2) * p.Bp)))
       return cudaErrorInvalidValue;
     TcJob &J = P.job[j];
+    J.has_lo = has_lo ? 1 : 0;
+    J.xparts = has_lo ? 3 : 2;
     J.rows = p.rows;
     J.M = h->M;
     J.Bp = p.Bp;
@@ -406,6 +435,7 @@ cudaError_t launch_multi(const JobSpec *jobs, int nj, const MultiPlan &mp, void 
   P.stages = mp.stages;
   P.chunk = mp.chunk;
   P.stage_bytes = mp.stage_bytes;
+  P.x_off = mp.x_off;
   P.status = reinterpret_cast<int *>(jobs[0].h->ws + jobs[0].h->status_off);
   if ((e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mp.smem)) !=
       cudaSuccess)
@@ -447,7 +477,7 @@ int psfsim_multi_validate(const psfsim_job_t *jobs, int njobs) {
     const psfsim_plan *h = jobs[j].plan;
     if (!h || !jobs[j].d_x || !jobs[j].d_y || jobs[j].capacity < 1 || jobs[j].capacity > kMaxBp)
       return PSFSIM_ERR_ARG;
-    if (h->storage != PSFSIM_SPLIT_BF16) return PSFSIM_ERR_UNSUPPORTED;
+    if (h->storage != PSFSIM_SPLIT_BF16 && h->storage != PSFSIM_BF16) return PSFSIM_ERR_UNSUPPORTED;
     if (h->device != jobs[0].plan->device) return PSFSIM_ERR_ARG;
   }
   return PSFSIM_OK;

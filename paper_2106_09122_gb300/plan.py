@@ -12,7 +12,7 @@ import torch
 
 from . import _binding as B
 
-_STORAGE = {"fp32": B.FP32, "split_bf16": B.SPLIT_BF16, "fp32_sym": B.FP32_SYM, "fused": B.FUSED}
+_STORAGE = {"fp32": B.FP32, "split_bf16": B.SPLIT_BF16, "bf16": B.BF16, "fp32_sym": B.FP32_SYM, "fused": B.FUSED}
 _INTERP = {"linear": B.LINEAR, "nearest": B.NEAREST}
 
 
@@ -127,14 +127,17 @@ class Plan:
         return flat.view(self.K, ld)[:, : self.M].t()
 
     def A_split(self):
-        """(hi [rows, ld] bf16, lo [rows, ld] bf16, scale [ld] f32) views of split-BF16 storage."""
-        if self.info.storage != B.SPLIT_BF16:
-            raise ValueError("A_split needs SPLIT_BF16 storage")
+        """(hi [rows, ld] bf16, lo [rows, ld] bf16 or None, scale [ld] f32) views of split-BF16
+        (or BF16: no lo) storage."""
+        if self.info.storage not in (B.SPLIT_BF16, B.BF16):
+            raise ValueError("A_split needs SPLIT_BF16 or BF16 storage")
         ld = self.info.ld
         rows = (self.M + 127) // 128 * 128
         nb = rows * ld * 2
         hi = self.workspace[self.info.a_offset:self.info.a_offset + nb].view(torch.bfloat16).view(rows, ld)
-        lo = self.workspace[self.info.lo_offset:self.info.lo_offset + nb].view(torch.bfloat16).view(rows, ld)
+        lo = None
+        if self.info.lo_offset >= 0:
+            lo = self.workspace[self.info.lo_offset:self.info.lo_offset + nb].view(torch.bfloat16).view(rows, ld)
         sc = self.workspace[self.info.scale_offset:self.info.scale_offset + ld * 4].view(torch.float32)
         return hi, lo, sc
 

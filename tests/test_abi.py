@@ -50,6 +50,9 @@ def test_workspace_bytes_covers_A(lib):
     assert out.value >= 128 * 128 * 128 * 128 * 4
     assert lib.psfsim_workspace_bytes(128, 40, 128 * 128, B.SPLIT_BF16, ctypes.byref(out)) == B.OK
     assert out.value >= 2 * 2 * 128 * 128 * 128 * 128
+    split = out.value
+    assert lib.psfsim_workspace_bytes(128, 40, 128 * 128, B.BF16, ctypes.byref(out)) == B.OK
+    assert 2 * 128 * 128 * 128 * 128 <= out.value < split - 128 ** 4  # hi alone: no lo array
     assert lib.psfsim_workspace_bytes(512, 80, 512 * 512, B.FUSED, ctypes.byref(out)) == B.OK
     assert 80 * 513 * 513 * 16 <= out.value < 500 * 2 ** 20
     assert lib.psfsim_workspace_bytes(0, 4, 10, B.FP32, ctypes.byref(out)) == B.ERR_ARG

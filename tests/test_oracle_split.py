@@ -31,3 +31,18 @@ def test_split_error_bound_and_scale():
 def test_pow2_scale(m):
     s = SO.pow2_scale_at_least(m)
     assert m <= s < 2 * m
+
+
+def test_bf16_hi_alone_error_bound_is_2_to_minus_8_and_attained():
+    """BF16 storage keeps hi alone: |sigma hi - A| <= 2^-8 |A| (round to nearest with an 8-bit
+    significand: half an ulp of 2^-7 relative spacing), and values near a rounding midpoint just
+    above a power of two come within 2% of that bound, so a row dominated by one element can
+    carry a bound-relative image error near 2^-8 (3.9e-3)."""
+    rng = np.random.default_rng(16)
+    A = (rng.uniform(0.0, 1.0, (4096, 8)) * 10.0 ** rng.uniform(-12, 0, (1, 8))).astype(np.float32)
+    scale = np.array([SO.pow2_scale_at_least(float(m)) for m in A.max(axis=0)])
+    hi, _ = SO.split_columns(A, scale)
+    dec = SO.decode(hi, np.zeros_like(hi), scale)
+    rel = np.abs(dec - A.astype(np.float64)) / np.abs(A.astype(np.float64))
+    assert rel.max() <= 2.0 ** -8
+    assert rel.max() >= 0.98 * 2.0 ** -8
