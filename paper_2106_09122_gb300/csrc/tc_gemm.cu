@@ -39,7 +39,7 @@ constexpr uint32_t kTileBytes = BM * BK * 2;
 constexpr int kMaxBp = 80;       // 3 * Bp <= 256 (MMA N and TMA box limits), Bp % 16 == 0
 constexpr int kMaxJobs = 16;
 constexpr int kDefaultChunk = 4; // k-tiles (of 64) per TMEM accumulation
-constexpr int kMaxChunk = 8;     // <= 64 accumulating MMAs between drains
+constexpr int kMaxMmas = 64;     // accumulating MMAs between drains (bounds the FP32 drift)
 
 // One product S_j = A_j Z_j of a (possibly multi-job) launch.
 struct TcJob {
@@ -392,7 +392,11 @@ MultiPlan plan_multi(const JobSpec *jobs, int nj, const psfsim_tuning_t *tune) {
   int fit = (int)((220 * 1024) / mp.stage_bytes);
   fit = fit > kMaxStages ? kMaxStages : fit;
   mp.stages = tune && tune->stages >= 2 && tune->stages < fit ? tune->stages : fit;
-  mp.chunk = tune && tune->chunk > 0 ? (tune->chunk > kMaxChunk ? kMaxChunk : tune->chunk) : kDefaultChunk;
+  // A k-tile is 4 MMAs per accumulator (8 with lo), so at most 16 (8) k-tiles
+  // accumulate between drains.
+  const int max_chunk = kMaxMmas / ((any_lo ? 2 : 1) * (BK / 16));
+  mp.chunk = tune && tune->chunk > 0 ? (tune->chunk > max_chunk ? max_chunk : tune->chunk)
+                                     : (any_lo ? kDefaultChunk : max_chunk);
   mp.smem = (size_t)mp.stages * mp.stage_bytes + 1024;
   return mp;
 }
