@@ -491,6 +491,40 @@ def _path_convolution(dev, stream):
     return out
 
 
+def _path_sparse(dev, stream, hbm):
+    """Skipping zero scene pixels (FP32 storage, 128^2 fit workload's A): the ring scene, which is
+    zero beyond the 12 lambda/D outer working angle, and ten point sources; each against the dense
+    forward.  Bytes are those of the columns actually read, never the dense A."""
+    import torch
+    from paper_2106_09122_gb300 import Plan
+    from synth import scenes, workloads
+    w = workloads.adjoint_128()
+    plan = Plan(torch.from_numpy(w.library().astype(np.float32)).to(dev), w.radii, w.s, N=w.N, S=w.S)
+    ring = scenes.ring_image(w.N, w.S, 5.0, 1.0, np.deg2rad(60.0), 0.3, 1e-9, w.r_max).astype(np.float32).ravel()
+    pts = np.zeros(w.K, dtype=np.float32)
+    rng = np.random.default_rng(93)
+    pts[rng.choice(np.nonzero(ring)[0], 10, replace=False)] = 1e-8
+    out = {"workload": "adjoint_fit_128 A (FP32, 1.07 GB): forward of one scene reading only the columns of "
+                       "non-zero scene pixels"}
+    for name, sc in (("ring_scene", ring), ("ten_point_sources", pts)):
+        x = torch.from_numpy(sc).to(dev)
+        y = torch.empty(w.M, device=dev)
+        nnz = int(np.count_nonzero(sc))
+        ms_s = _timed(lambda: plan.forward(x, out=y, skip_zeros=True), 50, stream)
+        ms_d = _timed(lambda: plan.forward(x, out=y), 50, stream)
+        ys = plan.forward(x, skip_zeros=True)
+        yd = plan.forward(x)
+        nbytes = nnz * w.M * 4 + w.K * 4 + w.M * 4
+        out[name] = {"nonzero_pixels": nnz, "images_per_s": 1e3 / ms_s, "ms": ms_s, "dense_ms": ms_d,
+                     "speedup_vs_dense": ms_d / ms_s,
+                     "max_rel_diff_vs_dense": float(((ys - yd).abs().max() / yd.abs().max()).item()),
+                     "roofline": {"bound": "hbm", "achieved": nbytes / (ms_s / 1e3) / 1e9, "peak": hbm,
+                                  "unit": "GB/s", "frac": nbytes / (ms_s / 1e3) / 1e9 / hbm,
+                                  "bytes_note": "columns of the non-zero pixels only"}}
+    plan.free()
+    return out
+
+
 def _path_fused(dev, stream, with_oracle):
     """Fused 512^2 workload: A (275 GB in FP32) regenerated on chip for 32 scenes."""
     import torch
@@ -872,6 +906,7 @@ def main():
             "batched_split_bf16_256_8_wavelengths": _path_batched(dev, stream, hbm, oracle_ok),
             "batched_bf16_256_8_wavelengths": _path_bf16(dev, stream, hbm, oracle_ok),
             "convolution_comparator_128": _path_convolution(dev, stream),
+            "skip_zero_pixels_128": _path_sparse(dev, stream, hbm),
             "fused_512": _path_fused(dev, stream, oracle_ok),
             "uneven_500": _path_uneven(dev, stream, hbm, oracle_ok),
             "nearest_vs_linear_128": _path_nearest(dev),

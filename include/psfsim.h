@@ -135,6 +135,17 @@ int psfsim_adjoint_scratch_bytes(psfsim_t h, int B, size_t *bytes);
 int psfsim_forward(psfsim_t h, const float *d_x, int B, float *d_y, void *d_scratch,
                    size_t scratch_bytes, void *stream);
 
+/* S = A Z (Eq. 6) reading only the columns of scene pixels that are non-zero
+ * in some scene of the batch (a zero pixel adds nothing to S): point sources,
+ * masked disks and everything beyond the outer working angle leave those
+ * columns unread.  FP32 storage only (else PSFSIM_ERR_UNSUPPORTED).  Same
+ * arguments and result as psfsim_forward, up to the order of the float32 sums;
+ * deterministic.  The list of columns is built on the device, so the call
+ * never synchronises. */
+int psfsim_forward_sparse_scratch_bytes(psfsim_t h, int B, size_t *bytes);
+int psfsim_forward_sparse(psfsim_t h, const float *d_x, int B, float *d_y, void *d_scratch,
+                          size_t scratch_bytes, void *stream);
+
 /* One product of a multi-job launch: S = A Z for up to 80 scenes of one
  * SPLIT_BF16 plan.  d_count (device int, may be NULL) holds how many of the
  * `capacity` scene slots are present in this call, so a captured CUDA graph

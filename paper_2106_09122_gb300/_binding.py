@@ -47,6 +47,8 @@ SIGNATURES = {
     "psfsim_forward_scratch_bytes": (i32, [vp, i32, c_size_p]),
     "psfsim_adjoint_scratch_bytes": (i32, [vp, i32, c_size_p]),
     "psfsim_forward": (i32, [vp, vp, i32, vp, vp, ctypes.c_size_t, vp]),
+    "psfsim_forward_sparse_scratch_bytes": (i32, [vp, i32, c_size_p]),
+    "psfsim_forward_sparse": (i32, [vp, vp, i32, vp, vp, ctypes.c_size_t, vp]),
     "psfsim_adjoint": (i32, [vp, vp, i32, vp, vp, ctypes.c_size_t, vp]),
     "psfsim_forward_static": (i32, [vp, vp, i32, vp, vp]),
     "psfsim_forward_multi_scratch_bytes": (i32, [ctypes.POINTER(Job), i32, ctypes.POINTER(Tuning), c_size_p]),

@@ -225,6 +225,24 @@ int psfsim_forward(psfsim_t h, const float *d_x, int B, float *d_y, void *d_scra
   return PSFSIM_ERR_UNSUPPORTED;
 }
 
+int psfsim_forward_sparse_scratch_bytes(psfsim_t h, int B, size_t *bytes) {
+  if (!h || !bytes || B < 1) return PSFSIM_ERR_ARG;
+  if (h->storage != PSFSIM_FP32) return PSFSIM_ERR_UNSUPPORTED;
+  *bytes = psfsim_forward_sparse_scratch(h, B);
+  return PSFSIM_OK;
+}
+
+int psfsim_forward_sparse(psfsim_t h, const float *d_x, int B, float *d_y, void *d_scratch, size_t scratch_bytes,
+                          void *stream) {
+  if (!h || !d_x || !d_y || B < 1) return PSFSIM_ERR_ARG;
+  if (h->storage != PSFSIM_FP32) return PSFSIM_ERR_UNSUPPORTED;
+  const size_t need = psfsim_forward_sparse_scratch(h, B);
+  if (!d_scratch || !aligned(d_scratch, 256) || scratch_bytes < need) return PSFSIM_ERR_WORKSPACE;
+  return psfsim_launch_forward_sparse(h, d_x, B, d_y, d_scratch, static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? PSFSIM_OK
+             : PSFSIM_ERR_CUDA;
+}
+
 int psfsim_adjoint(psfsim_t h, const float *d_g, int B, float *d_gx, void *d_scratch, size_t scratch_bytes,
                    void *stream) {
   if (!h || !d_g || !d_gx || B < 1) return PSFSIM_ERR_ARG;

@@ -63,6 +63,49 @@ __device__ __forceinline__ void fwd_accumulate(const float *__restrict__ A, int6
   }
 }
 
+// As fwd_accumulate<BB> over the listed columns idx[t0..t1) (ascending).
+template <int BB>
+__device__ __forceinline__ void fwd_accumulate_idx(const float *__restrict__ A, int64_t ld, int64_t K,
+                                                   const float *__restrict__ x, int b0, int64_t r,
+                                                   const int *__restrict__ idx, int64_t t0, int64_t t1,
+                                                   float (&acc)[BB][4]) {
+#pragma unroll
+  for (int b = 0; b < BB; ++b) acc[b][0] = acc[b][1] = acc[b][2] = acc[b][3] = 0.f;
+  const float *xb = x + (int64_t)b0 * K;
+  int64_t t = t0;
+  for (; t + 4 <= t1; t += 4) {
+    int j[4];
+    float4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) j[u] = __ldg(idx + t + u);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = ld_stream4(A + (int64_t)j[u] * ld + r);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+#pragma unroll
+      for (int b = 0; b < BB; ++b) {
+        const float xv = __ldg(xb + (int64_t)b * K + j[u]);
+        acc[b][0] = fmaf(v[u].x, xv, acc[b][0]);
+        acc[b][1] = fmaf(v[u].y, xv, acc[b][1]);
+        acc[b][2] = fmaf(v[u].z, xv, acc[b][2]);
+        acc[b][3] = fmaf(v[u].w, xv, acc[b][3]);
+      }
+    }
+  }
+  for (; t < t1; ++t) {
+    const int j = __ldg(idx + t);
+    const float4 v = ld_stream4(A + (int64_t)j * ld + r);
+#pragma unroll
+    for (int b = 0; b < BB; ++b) {
+      const float xv = __ldg(xb + (int64_t)b * K + j);
+      acc[b][0] = fmaf(v.x, xv, acc[b][0]);
+      acc[b][1] = fmaf(v.y, xv, acc[b][1]);
+      acc[b][2] = fmaf(v.z, xv, acc[b][2]);
+      acc[b][3] = fmaf(v.w, xv, acc[b][3]);
+    }
+  }
+}
+
 constexpr int kAdjThreads = 256;
 constexpr int kStashCols = 128;
 

@@ -56,6 +56,10 @@ cudaError_t psfsim_launch_build(psfsim_plan *h, cudaStream_t st);
 cudaError_t psfsim_launch_forward_fp32(const psfsim_plan *h, const float *x, int B, float *y,
                                        void *scratch, cudaStream_t st);
 size_t psfsim_forward_fp32_scratch(const psfsim_plan *h, int B);
+// FP32 forward over the scene pixels that are non-zero in some scene of the batch.
+size_t psfsim_forward_sparse_scratch(const psfsim_plan *h, int B);
+cudaError_t psfsim_launch_forward_sparse(const psfsim_plan *h, const float *x, int B, float *y, void *scratch,
+                                         cudaStream_t st);
 cudaError_t psfsim_launch_adjoint_fp32(const psfsim_plan *h, const float *g, int B, float *gx,
                                        cudaStream_t st);
 // y[b, i] = sum_ks part[(ks * B + b) * ld + i], fixed order.

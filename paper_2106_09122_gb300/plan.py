@@ -85,18 +85,21 @@ class Plan:
         return torch.empty(max(nbytes, 1), dtype=torch.uint8, device=self.lib.device)
 
     def forward(self, x: torch.Tensor, out: torch.Tensor | None = None, scratch: torch.Tensor | None = None,
-                stream=None) -> torch.Tensor:
-        """S = A Z for x of shape [K] or [B, K] (float32, CUDA)."""
+                stream=None, skip_zeros: bool = False) -> torch.Tensor:
+        """S = A Z for x of shape [K] or [B, K] (float32, CUDA).  skip_zeros (FP32 storage): read
+        only the columns of scene pixels that are non-zero in some scene (psfsim_forward_sparse)."""
         _dev_f32(x, "x")
         xb = x.view(-1, self.K)
         bsz = xb.shape[0]
         y = out if out is not None else torch.empty((bsz, self.M), dtype=torch.float32, device=x.device)
-        need = self.forward_scratch_bytes(bsz)
-        if scratch is None or scratch.numel() < need:
-            scratch = self._scratch(need)
-        B.check(self._lib.psfsim_forward(self.handle, ctypes.c_void_p(xb.data_ptr()), bsz,
+        name = "psfsim_forward_sparse" if skip_zeros else "psfsim_forward"
+        nb = ctypes.c_size_t()
+        B.check(getattr(self._lib, name + "_scratch_bytes")(self.handle, bsz, ctypes.byref(nb)), "scratch")
+        if scratch is None or scratch.numel() < nb.value:
+            scratch = self._scratch(nb.value)
+        B.check(getattr(self._lib, name)(self.handle, ctypes.c_void_p(xb.data_ptr()), bsz,
                                          ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(scratch.data_ptr()),
-                                         scratch.numel(), _stream_ptr(stream)), "psfsim_forward")
+                                         scratch.numel(), _stream_ptr(stream)), name)
         return y.view(self.M) if x.dim() == 1 else y
 
     def adjoint(self, g: torch.Tensor, out: torch.Tensor | None = None, scratch: torch.Tensor | None = None,
