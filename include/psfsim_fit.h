@@ -55,7 +55,11 @@ int psfsim_residual_loss(const float *d_y, const float *d_d, int64_t M, double s
  * The scene grid (N, S) is the plan's.  Same quantities as psfsim_ring_scene
  * + psfsim_forward + psfsim_residual_loss + psfsim_adjoint + psfsim_ring_chain,
  * deterministic, with sums in a different (fixed) order.
- * PSFSIM_ERR_UNSUPPORTED for other storages or point builds.  The two halves
+ * FP32_SYM plans (even N) take three launches: the forward leaves the four
+ * quarter-turned partial images, a second kernel sums them into S and forms r
+ * and the loss partials, and the adjoint scatters A^T r to the four turned
+ * pixels of each stored column.  PSFSIM_ERR_UNSUPPORTED for other storages or
+ * point builds.  The two halves
  * are also callable on their own (same scratch, same theta, in this order):
  * the first leaves the loss partials and dZ/dtheta in the scratch for the
  * second.  The scratch holds arrival counters: zero-fill it once before its

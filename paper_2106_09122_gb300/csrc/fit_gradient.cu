@@ -1,4 +1,5 @@
-// One fit gradient on an FP32 grid plan in two launches (include/psfsim_fit.h):
+// One fit gradient on an FP32 grid plan in two launches (include/psfsim_fit.h;
+// FP32_SYM plans are dispatched to fit_sym.cu):
 //
 //   fwd_ring_loss_kernel   Z = ring(theta) for each CTA's column range (kept
 //                          in shared memory; one tile per column also
@@ -310,22 +311,6 @@ GradScratch gradient_scratch(psfsim_plan *h) {
   return g;
 }
 
-// Launch configuration with programmatic stream serialization: the kernel may
-// be scheduled while the previous kernel in the stream finishes; it calls
-// griddep_wait before touching that kernel's results.
-cudaLaunchConfig_t pdl_config(dim3 grid, int threads, cudaStream_t st, cudaLaunchAttribute (&attr)[1]) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = dim3((unsigned)threads, 1, 1);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = st;
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cfg;
-}
-
 int gradient_args(psfsim_t h, double r_max, const double *h_theta, void *d_scratch, size_t scratch_bytes,
                   RingParams *P, GradScratch *g) {
   if (!h) return PSFSIM_ERR_ARG;
@@ -336,14 +321,23 @@ int gradient_args(psfsim_t h, double r_max, const double *h_theta, void *d_scrat
   return PSFSIM_OK;
 }
 
+// FP32_SYM: an even-N grid plan; the scratch must hold the symmetric layout.
+int sym_args(psfsim_t h, double r_max, const double *h_theta, void *d_scratch, size_t scratch_bytes, RingParams *P) {
+  if (h->N < 2 || (h->N & 1)) return PSFSIM_ERR_UNSUPPORTED;
+  if (!ring_params(h->N, h->S, r_max, h_theta, P)) return PSFSIM_ERR_ARG;
+  if (!d_scratch || !aligned256(d_scratch) || scratch_bytes < psfsim_sym_gradient_scratch(h))
+    return PSFSIM_ERR_WORKSPACE;
+  return PSFSIM_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 int psfsim_ring_gradient_scratch_bytes(psfsim_t h, size_t *bytes) {
   if (!h || !bytes) return PSFSIM_ERR_ARG;
-  if (h->storage != PSFSIM_FP32 || h->N < 1) return PSFSIM_ERR_UNSUPPORTED;
-  *bytes = gradient_scratch(h).total;
+  if (h->N < 1 || (h->storage != PSFSIM_FP32 && h->storage != PSFSIM_FP32_SYM)) return PSFSIM_ERR_UNSUPPORTED;
+  *bytes = h->storage == PSFSIM_FP32_SYM ? psfsim_sym_gradient_scratch(h) : gradient_scratch(h).total;
   return PSFSIM_OK;
 }
 
@@ -352,13 +346,20 @@ int psfsim_ring_forward_loss(psfsim_t h, double r_max, const double *h_theta, co
                              void *stream) {
   if (!d_target || !d_z || !d_y || !d_r || !(sigma > 0.0) || !std::isfinite(sigma)) return PSFSIM_ERR_ARG;
   RingParams P;
+  if (h && h->storage == PSFSIM_FP32_SYM) {
+    if (int rc = sym_args(h, r_max, h_theta, d_scratch, scratch_bytes, &P)) return rc;
+    return psfsim_sym_forward_loss(h, P, d_target, sigma, d_z, d_y, d_r, d_scratch,
+                                   static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? PSFSIM_OK
+               : PSFSIM_ERR_CUDA;
+  }
   GradScratch g;
   if (int rc = gradient_args(h, r_max, h_theta, d_scratch, scratch_bytes, &P, &g)) return rc;
   char *base = static_cast<char *>(d_scratch);
   unsigned *count = reinterpret_cast<unsigned *>(base + g.count);
   const float *A = reinterpret_cast<const float *>(h->ws + h->a_off);
   cudaLaunchAttribute attr[1];
-  const cudaLaunchConfig_t cfg = pdl_config(dim3((unsigned)forward_tiles(h), (unsigned)forward_splits(h)),
+  const cudaLaunchConfig_t cfg = psfsim_pdl_config(dim3((unsigned)forward_tiles(h), (unsigned)forward_splits(h)),
                                             kFwdThreads, static_cast<cudaStream_t>(stream), attr);
   const cudaError_t e = cudaLaunchKernelEx(
       &cfg, fwd_ring_loss_kernel, A, h->ld, h->M, h->K, P, d_z, reinterpret_cast<float *>(base + g.jac),
@@ -371,6 +372,13 @@ int psfsim_ring_adjoint_chain(psfsim_t h, double r_max, const double *h_theta, c
                               double *d_out, void *d_scratch, size_t scratch_bytes, void *stream) {
   if (!d_r || !d_gz || !d_out) return PSFSIM_ERR_ARG;
   RingParams P;
+  if (h && h->storage == PSFSIM_FP32_SYM) {
+    if (int rc = sym_args(h, r_max, h_theta, d_scratch, scratch_bytes, &P)) return rc;
+    return psfsim_sym_adjoint_chain(h, d_r, d_gz, d_out, d_scratch, static_cast<cudaStream_t>(stream)) ==
+                   cudaSuccess
+               ? PSFSIM_OK
+               : PSFSIM_ERR_CUDA;
+  }
   GradScratch g;
   if (int rc = gradient_args(h, r_max, h_theta, d_scratch, scratch_bytes, &P, &g)) return rc;
   char *base = static_cast<char *>(d_scratch);
@@ -385,7 +393,7 @@ int psfsim_ring_adjoint_chain(psfsim_t h, double r_max, const double *h_theta, c
                     d_out};
   cudaLaunchAttribute attr[1];
   const cudaLaunchConfig_t cfg =
-      pdl_config(dim3((unsigned)adjoint_blocks(h, vec)), kAdjThreads, static_cast<cudaStream_t>(stream), attr);
+      psfsim_pdl_config(dim3((unsigned)adjoint_blocks(h, vec)), kAdjThreads, static_cast<cudaStream_t>(stream), attr);
   const cudaError_t e = vec ? cudaLaunchKernelEx(&cfg, adj_chain_kernel<true>, A, h->ld, h->M, h->K, d_r, d_gz, c)
                             : cudaLaunchKernelEx(&cfg, adj_chain_kernel<false>, A, h->ld, h->M, h->K, d_r, d_gz, c);
   return e == cudaSuccess ? PSFSIM_OK : PSFSIM_ERR_CUDA;

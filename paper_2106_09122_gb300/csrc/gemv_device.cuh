@@ -21,8 +21,9 @@ constexpr int kRowsPerCta = kFwdThreads * 4;
 
 // acc[b][e] = sum_{j0 <= j < j1} A[r + e, j] x_b[j] for the thread's 4 rows,
 // where x_b[j] = x[(b0 + b) K + j] (kSmemX false: global scene vectors) or
-// x[j - j0] for b = 0 (kSmemX true: the range's scene values in shared memory).
-template <int BB, bool kSmemX = false>
+// x[b kXStride + j - j0] (kSmemX true: the range's scene values in shared
+// memory, kXStride apart).
+template <int BB, bool kSmemX = false, int kXStride = 0>
 __device__ __forceinline__ void fwd_accumulate(const float *__restrict__ A, int64_t ld, int64_t K,
                                                const float *__restrict__ x, int b0, int64_t r, int64_t j0,
                                                int64_t j1, float (&acc)[BB][4]) {
@@ -30,7 +31,7 @@ __device__ __forceinline__ void fwd_accumulate(const float *__restrict__ A, int6
   for (int b = 0; b < BB; ++b) acc[b][0] = acc[b][1] = acc[b][2] = acc[b][3] = 0.f;
   const float *a = A + j0 * ld + r;
   auto xval = [&](int b, int64_t j) -> float {
-    if (kSmemX) return x[j - j0];
+    if (kSmemX) return x[b * kXStride + (j - j0)];
     return __ldg(x + (int64_t)(b0 + b) * K + j);
   };
   int64_t j = j0;

@@ -99,3 +99,27 @@ cudaError_t psfsim_launch_adjoint_split(const psfsim_plan *h, const float *g, in
 
 static inline int64_t psfsim_round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
+// Launch configuration with programmatic stream serialization: the kernel may
+// be scheduled while the previous kernel in the stream finishes; it calls
+// griddep_wait before touching that kernel's results.
+inline cudaLaunchConfig_t psfsim_pdl_config(dim3 grid, int threads, cudaStream_t st, cudaLaunchAttribute (&attr)[1]) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3((unsigned)threads, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// Fit gradient on FP32_SYM storage (the compact quadrant matrix), three
+// launches; the C-ABI calls in fit_gradient.cu dispatch here.
+struct RingParams;
+size_t psfsim_sym_gradient_scratch(psfsim_plan *h);
+cudaError_t psfsim_sym_forward_loss(psfsim_plan *h, const RingParams &P, const float *d, double sigma, float *z,
+                                    float *y, float *r, void *scratch, cudaStream_t st);
+cudaError_t psfsim_sym_adjoint_chain(psfsim_plan *h, const float *r, float *gz, double *out, void *scratch,
+                                     cudaStream_t st);

@@ -49,8 +49,8 @@ class RingProblem:
         self.cscr = torch.empty(nb.value, **u8)
         B.check(self.lib.psfsim_loss_scratch_bytes(plan.M, ctypes.byref(nb)), "loss scratch")
         self.lscr = torch.empty(nb.value, **u8)
-        # FP32 grid plans take the fused path (two launches per gradient); its
-        # scratch holds arrival counters that must start at zero.
+        # FP32 grid plans take the fused path (two launches per gradient, three
+        # for FP32_SYM); its scratch holds arrival counters that must start at zero.
         self.fused = self.lib.psfsim_ring_gradient_scratch_bytes(plan.handle, ctypes.byref(nb)) == B.OK
         self.gscr = torch.zeros(max(nb.value, 256), **u8) if self.fused else None
         self.launches = 0
@@ -93,7 +93,7 @@ class RingProblem:
                                                   _vp(self.target), self.sigma, _vp(self.z), _vp(self.y), _vp(self.r),
                                                   _vp(self.gscr), self.gscr.numel(), _stream_ptr(None)),
                 "psfsim_ring_forward_loss")
-        self.launches += 1
+        self.launches += 2 if self.plan.storage == "fp32_sym" else 1
 
     def enqueue_adjoint_chain(self, theta) -> None:
         """Second half (one launch): A^T r, its dot with the stored Jacobian, the final sums into out6."""

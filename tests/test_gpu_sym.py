@@ -53,3 +53,37 @@ def test_sym_equals_dense_on_the_fit_workload():
     gd, gs = dense.adjoint(g), sym.adjoint(g)
     gbound = (Ad.abs().t() @ g.abs().t()).t()
     assert torch.all((gd - gs).abs() <= 2e-6 * gbound + 1e-30)
+
+
+@pytest.mark.parametrize("n,N", [(128, 128), (21, 20)])
+def test_sym_fit_gradient_matches_separate_operators_and_dense(n, N):
+    """psfsim_ring_gradient on FP32_SYM storage (three launches) against the same gradient
+    from the separate operators on the same plan, and against the dense FP32 plan; twice in a
+    row (counters back at zero, identical bits).  n = 21: odd image side (scalar adjoint path)."""
+    from paper_2106_09122_gb300.fit import RingProblem
+    S = 0.25
+    rng = np.random.default_rng(90 + n)
+    radii = np.linspace(0.0, 12.0 * N / 128.0 + 0.5, 12)
+    lib32 = (rng.uniform(0.0, 1.0, (12, n, n)) * 1e-3).astype(np.float32)
+    r_max = 0.95 * N * S / 2
+    sym = _plan(lib32, radii, 0.25, N=N, S=S, storage="fp32_sym")
+    dense = _plan(lib32, radii, 0.25, N=N, S=S)
+    d = torch.from_numpy((rng.uniform(0.5, 1.5, n * n) * 1e-12).astype(np.float32)).to(DEV)
+    theta = np.array([r_max / 2, r_max / 5, np.deg2rad(55.0), 0.3, 1e-9])
+    ps = RingProblem(sym, N, S, r_max, d, 1e-13)
+    pd = RingProblem(dense, N, S, r_max, d, 1e-13)
+    assert ps.fused and pd.fused
+    l1, g1 = ps.loss_and_grad(theta)
+    y1, gz1 = ps.y.clone(), ps.gz.clone()
+    l2, g2 = ps.loss_and_grad(theta)
+    assert l1 == l2 and np.array_equal(g1, g2)
+    ld, gd = pd.loss_and_grad(theta)
+    assert l1 == pytest.approx(ld, rel=1e-6)
+    np.testing.assert_allclose(g1, gd, rtol=1e-5, atol=1e-6 * np.abs(gd).max())
+    assert torch.allclose(y1, pd.y, rtol=1e-5, atol=0)
+    gzb = float(pd.gz.abs().max())
+    assert torch.all((gz1 - pd.gz).abs() <= 1e-5 * gzb)
+    ps.fused = False
+    l3, g3 = ps.loss_and_grad(theta)
+    assert l1 == pytest.approx(l3, rel=1e-6)
+    np.testing.assert_allclose(g1, g3, rtol=1e-5, atol=1e-6 * np.abs(g3).max())
