@@ -177,6 +177,66 @@ __global__ void __launch_bounds__(kLossThreads) sym_loss_kernel(const float *__r
   }
 }
 
+// gc[m][t] = sum_i A_Q0[i, t] gp[m][i] for t0 <= t < t1, two columns per pass
+// so that each load of the four turned residuals (from L2) serves both: the
+// four rotations would otherwise read four times the bytes of A from L2.
+// Rows split across the CTA (float4 strided), warp sums, then a fixed-order
+// sum over the warps through a double-buffered shared array.
+template <bool kVec>
+__device__ __forceinline__ void adj_pairs(const float *__restrict__ A, int64_t ld, int64_t M, int64_t Kv,
+                                          const float *__restrict__ gp, float *__restrict__ gc, int64_t t0,
+                                          int64_t t1) {
+  __shared__ float red[2][kAdjThreads / 32][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int parity = 0;
+  for (int64_t t = t0; t < t1; t += 2, parity ^= 1) {
+    const bool two = t + 1 < t1;
+    const float *c0 = A + t * ld;
+    const float *c1 = two ? c0 + ld : c0;
+    float acc[2][4] = {};
+    if (kVec) {
+      const int64_t M4 = M >> 2;
+      for (int64_t i4 = threadIdx.x; i4 < M4; i4 += kAdjThreads) {
+        const float4 v0 = ld_stream4(c0 + 4 * i4);
+        const float4 v1 = two ? ld_stream4(c1 + 4 * i4) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const float4 gv = __ldg(reinterpret_cast<const float4 *>(gp + (int64_t)b * M) + i4);
+          acc[0][b] = fmaf(v0.x, gv.x, fmaf(v0.y, gv.y, fmaf(v0.z, gv.z, fmaf(v0.w, gv.w, acc[0][b]))));
+          acc[1][b] = fmaf(v1.x, gv.x, fmaf(v1.y, gv.y, fmaf(v1.z, gv.z, fmaf(v1.w, gv.w, acc[1][b]))));
+        }
+      }
+    } else {
+      for (int64_t i = threadIdx.x; i < M; i += kAdjThreads) {
+        const float v0 = __ldg(c0 + i), v1 = two ? __ldg(c1 + i) : 0.f;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const float g = __ldg(gp + (int64_t)b * M + i);
+          acc[0][b] = fmaf(v0, g, acc[0][b]);
+          acc[1][b] = fmaf(v1, g, acc[1][b]);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        float s = acc[c][b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[parity][warp][c * 4 + b] = s;
+      }
+    __syncthreads();
+    if (threadIdx.x < (two ? 8 : 4)) {
+      const int c = threadIdx.x >> 2, b = threadIdx.x & 3;
+      float s = red[parity][0][threadIdx.x];
+#pragma unroll
+      for (int w = 1; w < kAdjThreads / 32; ++w) s += red[parity][w][threadIdx.x];
+      gc[(int64_t)b * Kv + t + c] = s;
+    }
+  }
+}
+
 struct SymChainArgs {
   const float *jac;         // dZ_j/dtheta_m at jac[m * K + j]
   double *chain_part;       // [gridDim.x][5]
@@ -188,7 +248,7 @@ struct SymChainArgs {
 };
 
 // CTA c: compact columns [Kv c / G, Kv (c+1) / G).  gc[m][t] = (A_Q0^T gp_m)_t
-// as adj_kernel<4>; then gz at the four turned pixels of each column and the
+// (adj_pairs); then gz at the four turned pixels of each column and the
 // FP64 chain partial sum_{t,m} gc[m][t] dZ/dtheta at that pixel (fixed thread
 // assignment, fixed tree); pixels whose quadrant column lies beyond the last
 // radius get gz = 0 (disjoint from the pixels the columns write).
@@ -201,7 +261,7 @@ __global__ void __launch_bounds__(kAdjThreads, 4)
   ptx::griddep_launch_dependents();
   ptx::griddep_wait();  // gp and dZ/dtheta come from the earlier kernels
   const int64_t t0 = Kv * blockIdx.x / gridDim.x, t1 = Kv * (blockIdx.x + 1) / gridDim.x;
-  adj_columns<4, kVec>(A, ld, M, Kv, gp, 0, gc, t0, t1);
+  adj_pairs<kVec>(A, ld, M, Kv, gp, gc, t0, t1);
   __syncthreads();  // this CTA's gc entries are written
   const int64_t K = (int64_t)N * N;
   double acc[5] = {0, 0, 0, 0, 0};
