@@ -863,6 +863,14 @@ def _profile_case(name: str) -> None:
         for _ in range(3):
             plan.forward(x)
             plan.adjoint(g)
+    elif name == "sparse128":
+        from synth import scenes
+        w = workloads.adjoint_128()
+        plan = Plan(torch.from_numpy(w.library().astype(np.float32)).to(dev), w.radii, w.s, N=w.N, S=w.S)
+        ring = scenes.ring_image(w.N, w.S, 5.0, 1.0, np.deg2rad(60.0), 0.3, 1e-9, w.r_max).astype(np.float32)
+        x = torch.from_numpy(ring.ravel()).to(dev)
+        for _ in range(3):
+            plan.forward(x, skip_zeros=True)
     elif name == "sym128":
         from paper_2106_09122_gb300.fit import RingProblem
         w = workloads.adjoint_128()
@@ -893,7 +901,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--main-only", action="store_true", help="skip the other workloads' measurements")
     ap.add_argument("--case", default=None,
-                    help="run one small profiling case (fp32_128, fit128, sym128, tc128, bf16_128, fused512)")
+                    help="run one small profiling case (fp32_128, fit128, sym128, sparse128, tc128, bf16_128, "
+                         "fused512)")
     args = ap.parse_args()
     if args.case:
         _profile_case(args.case)
