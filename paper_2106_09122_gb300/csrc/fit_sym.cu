@@ -196,16 +196,24 @@ __device__ __forceinline__ void adj_pairs(const float *__restrict__ A, int64_t l
     float acc[2][4] = {};
     if (kVec) {
       const int64_t M4 = M >> 2;
-      for (int64_t i4 = threadIdx.x; i4 < M4; i4 += kAdjThreads) {
-        const float4 v0 = ld_stream4(c0 + 4 * i4);
-        const float4 v1 = two ? ld_stream4(c1 + 4 * i4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      auto step = [&](const float4 &v0, const float4 &v1, int64_t i4) {
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
           const float4 gv = __ldg(reinterpret_cast<const float4 *>(gp + (int64_t)b * M) + i4);
           acc[0][b] = fmaf(v0.x, gv.x, fmaf(v0.y, gv.y, fmaf(v0.z, gv.z, fmaf(v0.w, gv.w, acc[0][b]))));
           acc[1][b] = fmaf(v1.x, gv.x, fmaf(v1.y, gv.y, fmaf(v1.z, gv.z, fmaf(v1.w, gv.w, acc[1][b]))));
         }
+      };
+      const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+      int64_t i4 = threadIdx.x;
+      for (; i4 + kAdjThreads < M4; i4 += 2 * kAdjThreads) {  // four A loads in flight per thread
+        const float4 a0 = ld_stream4(c0 + 4 * i4), b0 = ld_stream4(c0 + 4 * (i4 + kAdjThreads));
+        const float4 a1 = two ? ld_stream4(c1 + 4 * i4) : zero;
+        const float4 b1 = two ? ld_stream4(c1 + 4 * (i4 + kAdjThreads)) : zero;
+        step(a0, a1, i4);
+        step(b0, b1, i4 + kAdjThreads);
       }
+      for (; i4 < M4; i4 += kAdjThreads) step(ld_stream4(c0 + 4 * i4), two ? ld_stream4(c1 + 4 * i4) : zero, i4);
     } else {
       for (int64_t i = threadIdx.x; i < M; i += kAdjThreads) {
         const float v0 = __ldg(c0 + i), v1 = two ? __ldg(c1 + i) : 0.f;

@@ -107,9 +107,14 @@ class RingProblem:
     def enqueue_gradient(self, theta) -> None:
         """Ring -> forward -> loss and residual -> adjoint -> chain, all enqueued; the result lands
         in out6 = (loss, dL/dtheta)."""
-        if self.fused:
-            self.enqueue_forward_loss(theta)
-            self.enqueue_adjoint_chain(theta)
+        if self.fused:  # one C-ABI call enqueues both halves
+            th = np.ascontiguousarray(theta, dtype=np.float64)
+            B.check(self.lib.psfsim_ring_gradient(self.plan.handle, self.r_max, th.ctypes.data_as(ctypes.c_void_p),
+                                                  _vp(self.target), self.sigma, _vp(self.z), _vp(self.y),
+                                                  _vp(self.r), _vp(self.gz), _vp(self.out6), _vp(self.gscr),
+                                                  self.gscr.numel(), _stream_ptr(None)),
+                    "psfsim_ring_gradient")
+            self.launches += 3 if self.plan.storage == "fp32_sym" else 2
             return
         self.plan.forward(self.scene(theta), out=self.y, scratch=self.fscr)
         self.residual_loss(self.y, self.target, True)
