@@ -17,9 +17,10 @@
 // are summed in a fixed order afterwards.
 //
 // Warps: 0 TMA producer (x tiles), 1 tcgen05.mma issuer, 2..17 generators.
-// Generator warp w builds rows 32*(w%4).. and 16 columns of every 128 x 64
-// tile, and also drains the TMEM accumulator of rotation (w-2)/4 for those
-// rows into FP32 registers every kChunk k-tiles (the tensor core's FP32
+// Generator g = w - 2 builds 8 columns of a 64-row half of every 128 x 64
+// tile, two rows per lane (a column's entry and coordinates serve both), and
+// also drains the TMEM accumulator of rotation g/4 for rows 32*(w%4)..+31
+// into FP32 registers every kChunk k-tiles (the tensor core's FP32
 // accumulation is not round-to-nearest, so long accumulations drift).
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -137,14 +138,12 @@ __global__ void fused_xgather(const float *__restrict__ x, int B, int Bp, int N,
   }
 }
 
-// One A element from a column-table entry; (du2, dv2) = twice the pixel's
-// offset from the tile origin.  The 2 x 2 footprint of each PSF is one float4
-// of the quad-layout library, so only the footprint position needs a check.
+// One A element from a column-table entry and the pixel's fixed-point source
+// coordinates (a2, b2).  The 2 x 2 footprint of each PSF is one float4 of the
+// quad-layout library, so only the footprint position needs a check.
 __device__ __forceinline__ float gen_element(const ColEntry &e, const float4 *__restrict__ qlib, int n,
-                                             int64_t qsz, uint32_t du2, uint32_t dv2) {
+                                             int64_t qsz, long long a2, long long b2) {
   constexpr int kShift = PSFSIM_FRAC_BITS + 1;
-  const long long a2 = fx_mad(fx_mad(e.A0, e.Clo, e.Chi, du2), e.Slo, e.Shi, dv2);
-  const long long b2 = fx_mad(fx_mad(e.B0, e.NSlo, e.NShi, du2), e.Clo, e.Chi, dv2);
   const int q0 = (int)(a2 >> kShift);
   const int p0 = (int)(b2 >> kShift);
   if (e.off < 0 || q0 < -1 || q0 > n - 1 || p0 < -1 || p0 > n - 1) return 0.f;
@@ -304,12 +303,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int gtid = g * 32 + lane;      // 0..511
     const int quarter = warp & 3;        // TMEM lane quarter this warp may access
     const int rot = g >> 2;              // rotation whose accumulator columns this warp drains
-    const int cgrp = g >> 2;             // 16-column group this warp generates
-    const int r = quarter * 32 + lane;   // tile row
+    const int r = quarter * 32 + lane;   // tile row this lane drains
+    // Generation: this warp builds 8 columns (group g / 2) of the tile's 64-row
+    // half g % 2, two rows per lane: rA and rB = rA + 32, i.e. two image rows
+    // further down, whose source coordinates are rA's plus 2 (S, C) per column.
+    const int gc8 = g >> 1;
+    const int rA = 64 * (g & 1) + lane, rB = rA + 32;
     const int n = P.n;
     const long long h = n - 1;
     const long long base = h << PSFSIM_FRAC_BITS;
-    const uint32_t du2 = 2 * (r % kBlockQ), dv2 = 2 * (r / kBlockQ);
+    const uint32_t du2 = 2 * (rA % kBlockQ), dv2 = 2 * (rA / kBlockQ);
     uint32_t it = 0, c = 0, tg = 0;
     const ColEntry *cur = ctab[0];
     bool ok = true;
@@ -319,6 +322,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int po = (mt / P.tiles_q) * kBlockP, qo = (mt % P.tiles_q) * kBlockQ;
       const int p = po + r / kBlockQ, q = qo + r % kBlockQ;
       const bool row_ok = p < n && q < n;
+      const bool okA = po + rA / kBlockQ < n && qo + rA % kBlockQ < n;
+      const bool okB = po + rB / kBlockQ < n && qo + rB % kBlockQ < n;
       const long long uo = 2 * qo - h, vo = 2 * po - h;
       float sum[kMaxBp];
 #pragma unroll
@@ -390,27 +395,39 @@ __global__ void __launch_bounds__(kThreads, 1)
             continue;
           }
           uint8_t *st = smem + (size_t)s * P.stage_bytes;
-          uint32_t hw[8], lw[8];
+          uint32_t hw[2][4], lw[2][4];
 #pragma unroll
-          for (int cc = 0; cc < 16; cc += 2) {
-            float v0 = 0.f, v1 = 0.f;
-            if (row_ok) {
-              v0 = gen_element(tab[cgrp * 16 + cc], P.qlib, n, P.psz, du2, dv2);
-              v1 = gen_element(tab[cgrp * 16 + cc + 1], P.qlib, n, P.psz, du2, dv2);
+          for (int cc = 0; cc < 8; cc += 2) {
+            float vA[2], vB[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              const ColEntry &ce = tab[gc8 * 8 + cc + e];
+              const long long a2 = fx_mad(fx_mad(ce.A0, ce.Clo, ce.Chi, du2), ce.Slo, ce.Shi, dv2);
+              const long long b2 = fx_mad(fx_mad(ce.B0, ce.NSlo, ce.NShi, du2), ce.Clo, ce.Chi, dv2);
+              vA[e] = okA ? gen_element(ce, P.qlib, n, P.psz, a2, b2) : 0.f;
+              vB[e] = okB ? gen_element(ce, P.qlib, n, P.psz, fx_mad(a2, ce.Slo, ce.Shi, 4u),
+                                        fx_mad(b2, ce.Clo, ce.Chi, 4u))
+                          : 0.f;
             }
-            const uint32_t hp = pack_bf16(v0, v1);
-            hw[cc >> 1] = hp;
-            lw[cc >> 1] = pack_bf16(v0 - __uint_as_float(hp << 16), v1 - __uint_as_float(hp & 0xFFFF0000u));
+            uint32_t hp = pack_bf16(vA[0], vA[1]);
+            hw[0][cc >> 1] = hp;
+            lw[0][cc >> 1] =
+                pack_bf16(vA[0] - __uint_as_float(hp << 16), vA[1] - __uint_as_float(hp & 0xFFFF0000u));
+            hp = pack_bf16(vB[0], vB[1]);
+            hw[1][cc >> 1] = hp;
+            lw[1][cc >> 1] =
+                pack_bf16(vB[0] - __uint_as_float(hp << 16), vB[1] - __uint_as_float(hp & 0xFFFF0000u));
           }
           // 128-byte swizzle: 16-byte chunk index XOR (row % 8) inside each 1024-byte row group.
-          const uint32_t row_off = (uint32_t)(r >> 3) * 1024 + (uint32_t)(r & 7) * 128;
 #pragma unroll
-          for (int half = 0; half < 2; ++half) {
-            const uint32_t chunk = (uint32_t)(cgrp * 2 + half) ^ (uint32_t)(r & 7);
+          for (int hr = 0; hr < 2; ++hr) {
+            const int rr = hr ? rB : rA;
+            const uint32_t row_off = (uint32_t)(rr >> 3) * 1024 + (uint32_t)(rr & 7) * 128;
+            const uint32_t chunk = (uint32_t)gc8 ^ (uint32_t)(rr & 7);
             *reinterpret_cast<uint4 *>(st + row_off + chunk * 16) =
-                make_uint4(hw[4 * half], hw[4 * half + 1], hw[4 * half + 2], hw[4 * half + 3]);
+                make_uint4(hw[hr][0], hw[hr][1], hw[hr][2], hw[hr][3]);
             *reinterpret_cast<uint4 *>(st + kTileBytes + row_off + chunk * 16) =
-                make_uint4(lw[4 * half], lw[4 * half + 1], lw[4 * half + 2], lw[4 * half + 3]);
+                make_uint4(lw[hr][0], lw[hr][1], lw[hr][2], lw[hr][3]);
           }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           __syncwarp();
