@@ -60,7 +60,10 @@ enum psfsim_status {
  * CUDA-core adjoint).  FP32_SYM: FP32 columns of the x > 0, y > 0 quadrant only,
  * inside the last radius: the other three quadrants' columns are exact
  * quarter turns of these and the rest are zero (even N, grid builds only;
- * same results as FP32 up to the order of the sums).  FUSED: A is never
+ * same results as FP32 up to the order of the sums).  SPLIT_BF16_SYM: the
+ * same compaction of split-BF16 storage (tensor-core forward on the four
+ * rotated scenes at once; same results as SPLIT_BF16 up to the order of the
+ * sums).  FUSED: A is never
  * stored; tiles are regenerated from the library on every product (the
  * paper's "standard interpolation method", Table 4, done on chip). */
 enum psfsim_storage {
@@ -68,7 +71,8 @@ enum psfsim_storage {
   PSFSIM_SPLIT_BF16 = 1,
   PSFSIM_BF16 = 2,
   PSFSIM_FUSED = 3,
-  PSFSIM_FP32_SYM = 4
+  PSFSIM_FP32_SYM = 4,
+  PSFSIM_SPLIT_BF16_SYM = 5
 };
 
 /* Radial interpolation (Sec. 2 compares linear and nearest). */

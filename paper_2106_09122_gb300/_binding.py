@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpsfsim.so")
 
 OK, ERR_ARG, ERR_RADII, ERR_WORKSPACE, ERR_CUDA, ERR_UNSUPPORTED, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
-FP32, SPLIT_BF16, BF16, FUSED, FP32_SYM = 0, 1, 2, 3, 4
+FP32, SPLIT_BF16, BF16, FUSED, FP32_SYM, SPLIT_BF16_SYM = 0, 1, 2, 3, 4, 5
 LINEAR, NEAREST = 0, 1
 STATIC_SCRATCH_BYTES = 16 * 1024 * 1024
 

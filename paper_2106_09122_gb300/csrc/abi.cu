@@ -22,7 +22,7 @@ int check_radii(const double *r, int n_r) {
 
 bool storage_ok(int storage) {
   return storage == PSFSIM_FP32 || storage == PSFSIM_SPLIT_BF16 || storage == PSFSIM_BF16 ||
-         storage == PSFSIM_FP32_SYM || storage == PSFSIM_FUSED;
+         storage == PSFSIM_FP32_SYM || storage == PSFSIM_FUSED || storage == PSFSIM_SPLIT_BF16_SYM;
 }
 
 int common_build(const float *d_lib, const double *h_radii, int n_r, int n, double s, int N, double S,
@@ -36,7 +36,8 @@ int common_build(const float *d_lib, const double *h_radii, int n_r, int n, doub
   if (!aligned(d_lib, 16)) return PSFSIM_ERR_ARG;
   if (int rc = check_radii(h_radii, n_r)) return rc;
   // FUSED and FP32_SYM use the exact quarter-turn symmetry of an even N x N scene grid.
-  const bool quadrant = storage == PSFSIM_FUSED || storage == PSFSIM_FP32_SYM;
+  const bool quadrant =
+      storage == PSFSIM_FUSED || storage == PSFSIM_FP32_SYM || storage == PSFSIM_SPLIT_BF16_SYM;
   if (quadrant && (h_xy || N < 2 || (N & 1))) return PSFSIM_ERR_UNSUPPORTED;
   const WsLayout L = psfsim_layout(n, K, storage, n_r);
   if (!aligned(d_ws, 256) || ws_bytes < (size_t)L.total) return PSFSIM_ERR_WORKSPACE;
@@ -176,6 +177,10 @@ int psfsim_forward_scratch_bytes(psfsim_t h, int B, size_t *bytes) {
     *bytes = psfsim_forward_sym_scratch(h, B);
     return PSFSIM_OK;
   }
+  if (h->storage == PSFSIM_SPLIT_BF16_SYM) {
+    *bytes = psfsim_forward_split_sym_scratch(h, B);
+    return PSFSIM_OK;
+  }
   return PSFSIM_ERR_UNSUPPORTED;
 }
 
@@ -191,6 +196,10 @@ int psfsim_adjoint_scratch_bytes(psfsim_t h, int B, size_t *bytes) {
   }
   if (h->storage == PSFSIM_FP32_SYM) {
     *bytes = psfsim_adjoint_sym_scratch(h, B);
+    return PSFSIM_OK;
+  }
+  if (h->storage == PSFSIM_SPLIT_BF16_SYM) {
+    *bytes = psfsim_adjoint_split_sym_scratch(h, B);
     return PSFSIM_OK;
   }
   return PSFSIM_ERR_UNSUPPORTED;
@@ -215,6 +224,12 @@ int psfsim_forward(psfsim_t h, const float *d_x, int B, float *d_y, void *d_scra
     const size_t need = psfsim_forward_sym_scratch(h, B);
     if (!d_scratch || !aligned(d_scratch, 256) || scratch_bytes < need) return PSFSIM_ERR_WORKSPACE;
     return psfsim_launch_forward_sym(h, d_x, B, d_y, d_scratch, st) == cudaSuccess ? PSFSIM_OK : PSFSIM_ERR_CUDA;
+  }
+  if (h->storage == PSFSIM_SPLIT_BF16_SYM) {
+    const size_t need = psfsim_forward_split_sym_scratch(h, B);
+    if (!d_scratch || !aligned(d_scratch, 256) || scratch_bytes < need) return PSFSIM_ERR_WORKSPACE;
+    return psfsim_launch_forward_split_sym(h, d_x, B, d_y, d_scratch, st) == cudaSuccess ? PSFSIM_OK
+                                                                                         : PSFSIM_ERR_CUDA;
   }
   if (h->storage == PSFSIM_FUSED) {
     const size_t need = psfsim_forward_fused_scratch(h, B);
@@ -259,6 +274,12 @@ int psfsim_adjoint(psfsim_t h, const float *d_g, int B, float *d_gx, void *d_scr
     const size_t need = psfsim_adjoint_sym_scratch(h, B);
     if (!d_scratch || !aligned(d_scratch, 256) || scratch_bytes < need) return PSFSIM_ERR_WORKSPACE;
     return psfsim_launch_adjoint_sym(h, d_g, B, d_gx, d_scratch, st) == cudaSuccess ? PSFSIM_OK : PSFSIM_ERR_CUDA;
+  }
+  if (h->storage == PSFSIM_SPLIT_BF16_SYM) {
+    const size_t need = psfsim_adjoint_split_sym_scratch(h, B);
+    if (!d_scratch || !aligned(d_scratch, 256) || scratch_bytes < need) return PSFSIM_ERR_WORKSPACE;
+    return psfsim_launch_adjoint_split_sym(h, d_g, B, d_gx, d_scratch, st) == cudaSuccess ? PSFSIM_OK
+                                                                                          : PSFSIM_ERR_CUDA;
   }
   return PSFSIM_ERR_UNSUPPORTED;
 }

@@ -281,11 +281,12 @@ WsLayout psfsim_layout(int n, int64_t K, int storage, int n_r) {
     L.ld = psfsim_round_up(M, 32);
     // FP32_SYM stores at most the x > 0, y > 0 quadrant's columns.
     L.a_off = take(L.ld * (storage == PSFSIM_FP32_SYM ? (K + 3) / 4 : K) * 4);
-  } else if (storage == PSFSIM_SPLIT_BF16 || storage == PSFSIM_BF16) {
-    L.ld = psfsim_round_up(K, 64);
+  } else if (storage == PSFSIM_SPLIT_BF16 || storage == PSFSIM_BF16 || storage == PSFSIM_SPLIT_BF16_SYM) {
+    // SPLIT_BF16_SYM stores at most the x > 0, y > 0 quadrant's columns.
+    L.ld = psfsim_round_up(storage == PSFSIM_SPLIT_BF16_SYM ? (K + 3) / 4 : K, 64);
     const int64_t rows = psfsim_round_up(M, 128);
     L.a_off = take(rows * L.ld * 2);
-    if (storage == PSFSIM_SPLIT_BF16) L.lo_off = take(rows * L.ld * 2);
+    if (storage != PSFSIM_BF16) L.lo_off = take(rows * L.ld * 2);
     L.scale_off = take(L.ld * 4);
   } else {  // FUSED: nothing but the tables
     L.ld = 0;
@@ -356,7 +357,8 @@ cudaError_t psfsim_launch_build(psfsim_plan *h, cudaStream_t st) {
     h->K_valid = kv;
     if (h->storage == PSFSIM_FUSED) return psfsim_launch_quad_library(h, st);
   }
-  if (h->storage == PSFSIM_SPLIT_BF16 || h->storage == PSFSIM_BF16) return psfsim_launch_split_build(h, st);
+  if (h->storage == PSFSIM_SPLIT_BF16 || h->storage == PSFSIM_BF16 || h->storage == PSFSIM_SPLIT_BF16_SYM)
+    return psfsim_launch_split_build(h, st);
   if (h->storage != PSFSIM_FP32 && h->storage != PSFSIM_FP32_SYM) return cudaErrorNotSupported;
   const bool compact = h->storage == PSFSIM_FP32_SYM;
 

@@ -99,6 +99,17 @@ cudaError_t psfsim_launch_adjoint_split(const psfsim_plan *h, const float *g, in
 
 static inline int64_t psfsim_round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
+// Columns stored in A: the quadrant's valid columns for the compacted storages.
+static inline int64_t psfsim_cols(const psfsim_plan *h) { return h->quadrant ? h->K_valid : h->K; }
+
+// Split-BF16 storage compacted by the quarter-turn symmetry (sym.cu).
+size_t psfsim_forward_split_sym_scratch(const psfsim_plan *h, int B);
+cudaError_t psfsim_launch_forward_split_sym(const psfsim_plan *h, const float *x, int B, float *y, void *scratch,
+                                            cudaStream_t st);
+size_t psfsim_adjoint_split_sym_scratch(const psfsim_plan *h, int B);
+cudaError_t psfsim_launch_adjoint_split_sym(const psfsim_plan *h, const float *g, int B, float *gx, void *scratch,
+                                            cudaStream_t st);
+
 // Launch configuration with programmatic stream serialization: the kernel may
 // be scheduled while the previous kernel in the stream finishes; it calls
 // griddep_wait before touching that kernel's results.

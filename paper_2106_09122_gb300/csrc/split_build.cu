@@ -43,6 +43,7 @@ struct SplitParams {
   int n, pad;
   int64_t K, ld, M, rows;
   const ColGeom *geom;
+  const int *order;  // compacted storage: column j is geometry entry order[j] (else null: entry j)
   const float *lib;
   const float *libmax;
   __nv_bfloat16 *hi;
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(256) split_build_kernel(const SplitParams P) {
     const int64_t j = kt * kTileCols + jj;
     ColGeom g;
     g.k = -1;
-    if (j < P.K) g = P.geom[j];
+    if (j < P.K) g = P.geom[P.order ? P.order[j] : j];
     float inv = 1.f, sigma = 1.f;
     const float *L0 = P.lib, *L1 = P.lib;
     if (g.k >= 0) {
@@ -136,7 +137,8 @@ cudaError_t psfsim_launch_split_build(psfsim_plan *h, cudaStream_t st) {
   SplitParams P;
   P.n = h->n;
   P.pad = 0;
-  P.K = h->K;
+  P.K = psfsim_cols(h);
+  P.order = h->quadrant ? reinterpret_cast<const int *>(h->ws + h->order_off) : nullptr;
   P.ld = h->ld;
   P.M = h->M;
   P.rows = psfsim_round_up(h->M, kTileRows);

@@ -138,5 +138,5 @@ cudaError_t psfsim_launch_adjoint_split(const psfsim_plan *h, const float *g, in
     else { e = group<1>(h, g, B, b0, part, KS, st); b0 += 1; }
   }
   if (e != cudaSuccess) return e;
-  return psfsim_launch_reduce_partials(part, KS, B, h->ld, h->K, gx, nullptr, st);
+  return psfsim_launch_reduce_partials(part, KS, B, h->ld, psfsim_cols(h), gx, nullptr, st);
 }

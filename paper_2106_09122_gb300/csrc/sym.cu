@@ -154,3 +154,53 @@ cudaError_t psfsim_launch_adjoint_sym(const psfsim_plan *h, const float *g, int 
   sym_scatter<<<grid_for((int64_t)4 * B * h->K_valid, h->num_sms), 256, 0, st>>>(gc, B, h->N, h->K_valid, order, gx);
   return cudaGetLastError();
 }
+
+// ---- split-BF16 storage with the same compaction (PSFSIM_SPLIT_BF16_SYM) ----
+// Forward: the four rotated scenes of every scene are gathered as a batch of
+// 4B for the tcgen05 product over the compact columns, and the 4B partial
+// images are summed through the inverse quarter turns.  Adjoint: the residual
+// turned four ways, the split adjoint over the compact columns, and a scatter
+// to the four rotated scene pixels.
+
+size_t psfsim_forward_split_sym_scratch(const psfsim_plan *h, int B) {
+  return (size_t)psfsim_round_up((int64_t)4 * B * h->ld * 4, 256) +
+         (size_t)psfsim_round_up((int64_t)4 * B * h->M * 4, 256) + psfsim_forward_tc_scratch(h, 4 * B);
+}
+
+cudaError_t psfsim_launch_forward_split_sym(const psfsim_plan *h, const float *x, int B, float *y, void *scratch,
+                                            cudaStream_t st) {
+  const int *order = reinterpret_cast<const int *>(h->ws + h->order_off);
+  const int64_t Kv = h->K_valid;
+  float *xc = static_cast<float *>(scratch);
+  float *v = reinterpret_cast<float *>(static_cast<char *>(scratch) + psfsim_round_up((int64_t)4 * B * h->ld * 4, 256));
+  void *tc = reinterpret_cast<char *>(v) + psfsim_round_up((int64_t)4 * B * h->M * 4, 256);
+  if (Kv == 0) return cudaMemsetAsync(y, 0, (size_t)B * h->M * 4, st);
+  sym_gather<<<grid_for((int64_t)4 * B * Kv, h->num_sms), 256, 0, st>>>(x, B, h->N, Kv, order, xc);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if ((e = psfsim_launch_forward_tc(h, xc, 4 * B, v, tc, st)) != cudaSuccess) return e;
+  sym_permsum<<<grid_for((int64_t)B * h->M, h->num_sms), 256, 0, st>>>(v, B, h->n, y);
+  return cudaGetLastError();
+}
+
+size_t psfsim_adjoint_split_sym_scratch(const psfsim_plan *h, int B) {
+  return (size_t)psfsim_round_up((int64_t)4 * B * h->M * 4, 256) +
+         (size_t)psfsim_round_up((int64_t)4 * B * (h->K_valid > 0 ? h->K_valid : 1) * 4, 256) +
+         psfsim_adjoint_split_scratch(h, 4 * B);
+}
+
+cudaError_t psfsim_launch_adjoint_split_sym(const psfsim_plan *h, const float *g, int B, float *gx, void *scratch,
+                                            cudaStream_t st) {
+  const int *order = reinterpret_cast<const int *>(h->ws + h->order_off);
+  const int64_t Kv = h->K_valid;
+  float *gp = static_cast<float *>(scratch);
+  float *gc = reinterpret_cast<float *>(static_cast<char *>(scratch) + psfsim_round_up((int64_t)4 * B * h->M * 4, 256));
+  void *part = reinterpret_cast<char *>(gc) + psfsim_round_up((int64_t)4 * B * (Kv > 0 ? Kv : 1) * 4, 256);
+  cudaError_t e = cudaMemsetAsync(gx, 0, (size_t)B * h->K * 4, st);
+  if (e != cudaSuccess || Kv == 0) return e;
+  sym_gperm<<<grid_for((int64_t)4 * B * h->M, h->num_sms), 256, 0, st>>>(g, B, h->n, gp);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = psfsim_launch_adjoint_split(h, gp, 4 * B, gc, part, st)) != cudaSuccess) return e;
+  sym_scatter<<<grid_for((int64_t)4 * B * Kv, h->num_sms), 256, 0, st>>>(gc, B, h->N, Kv, order, gx);
+  return cudaGetLastError();
+}

@@ -411,7 +411,8 @@ cudaError_t launch_multi(const JobSpec *jobs, int nj, const MultiPlan &mp, void 
     const JobPlan &p = mp.jp[j];
     __nv_bfloat16 *xs = reinterpret_cast<__nv_bfloat16 *>(base + p.xs_off);
     const float *scale = reinterpret_cast<const float *>(h->ws + h->scale_off);
-    xsplit_kernel<<<h->num_sms * 4, 256, 0, st>>>(jobs[j].x, jobs[j].cap, jobs[j].count, p.Bp, h->K, h->ld, scale,
+    xsplit_kernel<<<h->num_sms * 4, 256, 0, st>>>(jobs[j].x, jobs[j].cap, jobs[j].count, p.Bp, psfsim_cols(h), h->ld,
+                                                  scale,
                                                   xs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const bool has_lo = h->lo_off >= 0;
@@ -467,7 +468,7 @@ cudaError_t psfsim_launch_forward_tc(const psfsim_plan *h, const float *x, int B
                                      cudaStream_t st) {
   for (int b0 = 0; b0 < B; b0 += kMaxBp) {
     const int Bc = (B - b0) < kMaxBp ? (B - b0) : kMaxBp;
-    JobSpec js{h, x + (int64_t)b0 * h->K, y + (int64_t)b0 * h->M, Bc, nullptr};
+    JobSpec js{h, x + (int64_t)b0 * psfsim_cols(h), y + (int64_t)b0 * h->M, Bc, nullptr};
     const MultiPlan mp = plan_multi(&js, 1, nullptr);
     cudaError_t e = launch_multi(&js, 1, mp, scratch, st);
     if (e != cudaSuccess) return e;

@@ -12,7 +12,8 @@ import torch
 
 from . import _binding as B
 
-_STORAGE = {"fp32": B.FP32, "split_bf16": B.SPLIT_BF16, "bf16": B.BF16, "fp32_sym": B.FP32_SYM, "fused": B.FUSED}
+_STORAGE = {"fp32": B.FP32, "split_bf16": B.SPLIT_BF16, "bf16": B.BF16, "fp32_sym": B.FP32_SYM, "fused": B.FUSED,
+            "split_bf16_sym": B.SPLIT_BF16_SYM}
 _INTERP = {"linear": B.LINEAR, "nearest": B.NEAREST}
 
 
@@ -132,8 +133,8 @@ class Plan:
     def A_split(self):
         """(hi [rows, ld] bf16, lo [rows, ld] bf16 or None, scale [ld] f32) views of split-BF16
         (or BF16: no lo) storage."""
-        if self.info.storage not in (B.SPLIT_BF16, B.BF16):
-            raise ValueError("A_split needs SPLIT_BF16 or BF16 storage")
+        if self.info.storage not in (B.SPLIT_BF16, B.BF16, B.SPLIT_BF16_SYM):
+            raise ValueError("A_split needs SPLIT_BF16, BF16 or SPLIT_BF16_SYM storage")
         ld = self.info.ld
         rows = (self.M + 127) // 128 * 128
         nb = rows * ld * 2

@@ -53,6 +53,8 @@ def test_workspace_bytes_covers_A(lib):
     split = out.value
     assert lib.psfsim_workspace_bytes(128, 40, 128 * 128, B.BF16, ctypes.byref(out)) == B.OK
     assert 2 * 128 * 128 * 128 * 128 <= out.value < split - 128 ** 4  # hi alone: no lo array
+    assert lib.psfsim_workspace_bytes(128, 40, 128 * 128, B.SPLIT_BF16_SYM, ctypes.byref(out)) == B.OK
+    assert 4 * 128 * 128 * 128 * 128 // 4 <= out.value < split // 3  # hi + lo of the quadrant's columns
     assert lib.psfsim_workspace_bytes(512, 80, 512 * 512, B.FUSED, ctypes.byref(out)) == B.OK
     assert 80 * 513 * 513 * 16 <= out.value < 500 * 2 ** 20
     assert lib.psfsim_workspace_bytes(0, 4, 10, B.FP32, ctypes.byref(out)) == B.ERR_ARG
@@ -87,6 +89,7 @@ def test_build_rejects_bad_arguments_before_launch(lib):
 def test_symmetric_storages_need_an_even_scene_grid(lib):
     assert _build(lib, [0.0, 1.0, 2.0], N=9, storage=B.FUSED)[0] == B.ERR_UNSUPPORTED
     assert _build(lib, [0.0, 1.0, 2.0], N=9, storage=B.FP32_SYM)[0] == B.ERR_UNSUPPORTED
+    assert _build(lib, [0.0, 1.0, 2.0], N=9, storage=B.SPLIT_BF16_SYM)[0] == B.ERR_UNSUPPORTED
 
 
 def test_products_reject_null_handles(lib):

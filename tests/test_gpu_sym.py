@@ -87,3 +87,28 @@ def test_sym_fit_gradient_matches_separate_operators_and_dense(n, N):
     l3, g3 = ps.loss_and_grad(theta)
     assert l1 == pytest.approx(l3, rel=1e-6)
     np.testing.assert_allclose(g1, g3, rtol=1e-5, atol=1e-6 * np.abs(g3).max())
+
+
+@pytest.mark.parametrize("n,N,S,B", [(20, 16, 0.35, 3), (24, 30, 0.2, 23), (15, 10, 0.5, 1)])
+def test_split_sym_forward_adjoint_match_oracle(n, N, S, B):
+    """SPLIT_BF16_SYM: the quadrant's split-BF16 columns; the four rotated scenes ride as a batch
+    of 4B through the tcgen05 product (B = 23: 92 rotated scenes, two launches of the product)."""
+    rng = np.random.default_rng(3 * n + N + B)
+    radii = np.sort(rng.uniform(0.0, 3.5, 8))
+    radii[0] = 0.0
+    lib32 = rng.uniform(0.0, 1.0, (8, n, n)).astype(np.float32)
+    plan = _plan(lib32, radii, 0.5, N=N, S=S, storage="split_bf16_sym")
+    assert plan.info.K_stored < N * N // 4 + 1
+    A = O.build_A(lib32.astype(np.float64), radii, N, S)
+    x = rng.uniform(0.0, 1.0, (B, N * N)).astype(np.float32)
+    y = plan.forward(torch.from_numpy(x).to(DEV)).double().cpu().numpy()
+    assert plan.sync_status() == 0
+    for b in range(B):
+        x64 = x[b].astype(np.float64)
+        rel = O.bound_relative_error(y[b], A @ x64, np.abs(A) @ np.abs(x64), floor=O.FLT_MIN)
+        assert rel.max() <= 1e-5, (b, rel.max())
+    g = rng.standard_normal((2, n * n)).astype(np.float32)
+    gx = plan.adjoint(torch.from_numpy(g).to(DEV)).double().cpu().numpy()
+    ref = O.adjoint(A, g.astype(np.float64))
+    bound = O.adjoint(np.abs(A), np.abs(g.astype(np.float64)))
+    assert np.all(np.abs(gx - ref) <= 1e-5 * bound + 1e-30)
