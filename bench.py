@@ -385,6 +385,60 @@ def _path_batched(dev, stream, hbm, with_oracle):
     return out
 
 
+def _path_split_sym(dev, stream, hbm, with_oracle):
+    """The batched 256^2 workload (8 wavelengths x 64 scenes) on split-BF16 storage compacted by
+    the quarter-turn symmetry and the zero columns; one forward per wavelength (the four rotations
+    of the 64 scenes as 256 scenes of the tcgen05 product).  Bytes are those of the compact A."""
+    import torch
+    from paper_2106_09122_gb300 import Plan
+    from synth import workloads
+    w = workloads.batched_256()
+    nl, B = len(w.lam_ratios), w.extra["scenes"]
+    libs = [w.library(l).astype(np.float32) for l in range(nl)]
+    plans = [Plan(torch.from_numpy(lb).to(dev), w.radii, w.s, N=w.N, S=w.S, storage="split_bf16_sym") for lb in libs]
+    X_np, X, Y = [], [], []
+    for l in range(nl):
+        xs = np.empty((B, w.K), dtype=np.float32)
+        for b in range(B):
+            xs[b] = workloads.random_ring_scene(w.N, w.S, w.r_max, w.seed + 100000 * (l + 1) + b).ravel()
+        X_np.append(xs)
+        X.append(torch.from_numpy(xs).to(dev))
+        Y.append(torch.empty((B, w.M), device=dev))
+    scr = torch.empty(plans[0].forward_scratch_bytes(B), dtype=torch.uint8, device=dev)
+
+    def run():
+        for l in range(nl):
+            plans[l].forward(X[l], out=Y[l], scratch=scr)
+
+    ms = _timed(run, 10, stream)
+    kst = plans[0].info.K_stored
+    ld = plans[0].info.ld
+    rows = (w.M + 127) // 128 * 128
+    passes = -(-4 * B // 80)      # the product takes at most 80 scenes per pass over A
+    a_bytes = nl * passes * (4 * rows * ld)
+    out = {"workload": "batched_split_bf16_sym_256: the batched 256^2 workload (8 wavelengths x 64 scenes) on "
+                       f"split-BF16 storage of the quadrant's columns inside 12 lambda/D ({kst} of {w.K} columns, "
+                       f"8 x {4 * rows * ld / 1e9:.2f} GB)",
+           "images_per_s": nl * B / (ms / 1e3), "ms_per_batch": ms,
+           "roofline": {"bound": "hbm", "achieved": a_bytes / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                        "frac": a_bytes / (ms / 1e3) / 1e9 / hbm,
+                        "kernel": "gather + tc_gemm_kernel over the compact A (256 rotated scenes) + turned sum",
+                        "bytes_note": "compact A read once per pass of at most 80 rotated scenes "
+                                      f"({passes} passes), not the dense A"},
+           "status": plans[0].sync_status()}
+    if with_oracle:
+        per = []
+        for l in range(nl):
+            rows_c = np.sort(np.random.default_rng(97 + l).choice(w.M, 12, replace=False))
+            Yr = Y[l][:4, torch.from_numpy(rows_c).to(dev)].cpu().numpy()
+            per.append(_rows_error(libs[l], w.radii, w.N, w.S, X_np[l][:4], Yr, rows_c)["max_bound_rel_error"])
+        out["error_vs_oracle_per_wavelength"] = {"max_bound_rel_error": per, "rows_per_wavelength": 12,
+                                                 "scenes_per_wavelength": 4}
+    del plans, X, Y
+    torch.cuda.empty_cache()
+    return out
+
+
 def _path_bf16(dev, stream, hbm, with_oracle):
     """The batched 256^2 workload with plain BF16 storage (hi alone: 8 x 8.6 GB), one multi-job
     tcgen05 launch: half the bytes of split-BF16 at 2^-8 instead of 2^-17 storage error."""
@@ -931,6 +985,7 @@ def main():
         out["other_workloads"] = {
             "batched_split_bf16_256_8_wavelengths": _path_batched(dev, stream, hbm, oracle_ok),
             "batched_bf16_256_8_wavelengths": _path_bf16(dev, stream, hbm, oracle_ok),
+            "batched_split_bf16_sym_256_8_wavelengths": _path_split_sym(dev, stream, hbm, oracle_ok),
             "convolution_comparator_128": _path_convolution(dev, stream),
             "skip_zero_pixels_128": _path_sparse(dev, stream, hbm),
             "fused_512": _path_fused(dev, stream, oracle_ok),

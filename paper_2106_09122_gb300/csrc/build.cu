@@ -356,6 +356,9 @@ cudaError_t psfsim_launch_build(psfsim_plan *h, cudaStream_t st) {
       return e;
     h->K_valid = kv;
     if (h->storage == PSFSIM_FUSED) return psfsim_launch_quad_library(h, st);
+    // Compact split-BF16 rows hold just the valid columns (the layout reserved
+    // the whole quadrant, an upper bound, before the count was known).
+    if (h->storage == PSFSIM_SPLIT_BF16_SYM) h->ld = psfsim_round_up(kv > 0 ? kv : 1, 64);
   }
   if (h->storage == PSFSIM_SPLIT_BF16 || h->storage == PSFSIM_BF16 || h->storage == PSFSIM_SPLIT_BF16_SYM)
     return psfsim_launch_split_build(h, st);
