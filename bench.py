@@ -231,6 +231,26 @@ def _gpu_arm(args, rank, world, local_rank):
     e2e_ms = _allreduce_max(e2e_ms, dev)
     e2e_out = hout.numpy().copy()
 
+    # the same, with no staging copies: the forward kernel reads the target
+    # straight from pinned (mapped) host memory and the adjoint writes the loss
+    # and gradient straight into it, over the CPU-GPU link, so that nothing
+    # stands between one gradient's kernels and the next
+    hd_m = d.cpu().pin_memory()
+    hout_m = torch.zeros(6, dtype=torch.float64).pin_memory()
+    prob_m = RingProblem(plan, w.N, w.S, w.r_max, hd_m, sigma)
+    prob_m.out6 = hout_m
+    prob_m.loss_d, prob_m.dtheta = hout_m[:1], hout_m[1:]
+    for _ in range(args.warmup):
+        prob_m.enqueue_gradient(theta)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(nsteps):
+        prob_m.enqueue_gradient(theta)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_mapped_ms = _allreduce_max(e0.elapsed_time(e1), dev)
+    e2e_mapped_out = hout_m.numpy().copy()
+
     # plain FP32 GEMV comparator (cuBLAS through torch) on the same stored A
     x = torch.from_numpy(x_np).to(dev)
     g = torch.from_numpy(g_np).to(dev)
@@ -300,9 +320,17 @@ def _gpu_arm(args, rank, world, local_rank):
         "fit": {"steps": int(len(hist) - 1), "seconds": fit_s, "loss_first": float(hist[0]),
                 "loss_last": float(hist[-1]), "theta": [float(v) for v in theta_fit],
                 "truth": [float(v) for v in truth]},
-        "e2e": {"value": images / (e2e_ms / 1e3), "unit": "images/s",
+        "e2e": {"value": images / (e2e_mapped_ms / 1e3), "unit": "images/s",
                 "h2d_bytes_per_step": w.M * 4, "d2h_bytes_per_step": 6 * 8,
-                "result_equals_device_path": bool(np.array_equal(e2e_out, dev_out6))},
+                "result_equals_device_path": bool(np.array_equal(e2e_mapped_out, dev_out6)),
+                "transfer": "every step the forward kernel reads the new target (64 KB) from pinned host memory "
+                            "and the adjoint writes the loss and gradient (48 B) into pinned host memory, both "
+                            "mapped into the GPU's address space (no staging copies)"},
+        "e2e_staged": {"value": images / (e2e_ms / 1e3), "unit": "images/s",
+                       "h2d_bytes_per_step": w.M * 4, "d2h_bytes_per_step": 6 * 8,
+                       "result_equals_device_path": bool(np.array_equal(e2e_out, dev_out6)),
+                       "transfer": "cudaMemcpyAsync of the target from pinned host memory into device memory "
+                                   "before each gradient, of the loss and gradient back after it"},
         "gpu_launches": launches,
         "clocks": clk,
     }

@@ -63,7 +63,10 @@ int psfsim_residual_loss(const float *d_y, const float *d_d, int64_t M, double s
  * are also callable on their own (same scratch, same theta, in this order):
  * the first leaves the loss partials and dZ/dtheta in the scratch for the
  * second.  The scratch holds arrival counters: zero-fill it once before its
- * first use; every call leaves the counters at zero again. */
+ * first use; every call leaves the counters at zero again.  d_target and
+ * d_out may also be pinned host memory mapped into the device's address
+ * space: the kernels then read the target and write the result across the
+ * CPU-GPU link, with no copy between consecutive gradients. */
 int psfsim_ring_gradient_scratch_bytes(psfsim_t h, size_t *bytes);
 int psfsim_ring_forward_loss(psfsim_t h, double r_max, const double *h_theta, const float *d_target, double sigma,
                              float *d_z, float *d_y, float *d_r, void *d_scratch, size_t scratch_bytes,
