@@ -162,3 +162,23 @@ def test_fused_gradient_on_ragged_shapes_repeats_and_matches_separate(n, N):
     assert torch.allclose(P.y, y_f, rtol=1e-6, atol=0)
     assert loss_f == pytest.approx(loss_s, rel=1e-6)
     np.testing.assert_allclose(g_f, g_s, rtol=1e-5, atol=1e-6 * np.abs(g_s).max())
+
+
+def test_gradient_reads_target_and_writes_result_in_pinned_host_memory():
+    """psfsim_ring_gradient with the target and the result in pinned host memory (mapped into
+    the device's address space): the same bits as with both in device memory."""
+    w = workloads.adjoint_128()
+    lib32 = w.library().astype(np.float32)
+    rng = np.random.default_rng(36)
+    d32 = (rng.uniform(0.5, 1.5, w.M) * 1e-10).astype(np.float32)
+    P = _problem(lib32, w.radii, w.s, w.N, w.S, w.r_max, d32, w.extra["sigma"])
+    from paper_2106_09122_gb300.fit import RingProblem
+    host_d = torch.from_numpy(d32).pin_memory()
+    Q = RingProblem(P.plan, w.N, w.S, w.r_max, host_d, w.extra["sigma"])
+    out = torch.zeros(6, dtype=torch.float64).pin_memory()
+    Q.out6, Q.loss_d, Q.dtheta = out, out[:1], out[1:]
+    theta = np.array(w.extra["truth"]) * np.array([1.02, 0.97, 1.01, 1.05, 1.1])
+    l_dev, g_dev = P.loss_and_grad(theta)
+    Q.enqueue_gradient(theta)
+    torch.cuda.synchronize()
+    assert out[0].item() == l_dev and np.array_equal(out[1:].numpy(), g_dev)
