@@ -60,6 +60,7 @@ struct TcMulti {
   int njobs, units, stages, chunk;
   uint32_t stage_bytes;
   uint32_t x_off;  // byte offset of the x tile in a stage: after hi and lo, or after hi alone
+  int interleave;  // jobs share one A and one unit count: unit u is job u % njobs, unit u / njobs
   int *status;
 };
 
@@ -90,6 +91,20 @@ __device__ __forceinline__ int find_job(const TcMulti &P, int u) {
   int j = 0;
   while (j + 1 < P.njobs && u >= P.job[j + 1].unit_begin) ++j;
   return j;
+}
+
+// Work unit u -> (job, unit within the job).  Interleaved jobs (several scene
+// blocks against one A) put the same (m-tile, k-range) of every job on
+// neighbouring units, so CTAs running together read the same A tiles and L2
+// serves all but the first read.
+__device__ __forceinline__ void unit_of(const TcMulti &P, int u, int &jb, int &lu) {
+  if (P.interleave) {
+    jb = u % P.njobs;
+    lu = u / P.njobs;
+  } else {
+    jb = find_job(P, u);
+    lu = u - P.job[jb].unit_begin;
+  }
 }
 
 __device__ __forceinline__ int k_begin(const TcJob &J, int ks) { return (int)((int64_t)J.k_tiles * ks / J.KS); }
@@ -128,9 +143,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     uint32_t it = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < P.units && ok && !abort_flag; u += gridDim.x) {
-      const int jb = find_job(P, u);
+      int jb, lu;
+      unit_of(P, u, jb, lu);
       const TcJob &J = P.job[jb];
-      const int lu = u - J.unit_begin;
       const int ks = lu / J.m_tiles, mt = lu % J.m_tiles;
       const uint32_t tx = (J.has_lo ? 2 : 1) * kTileBytes + (uint32_t)(J.xparts * J.Bp) * BK * 2;
       for (int kt = k_begin(J, ks); kt < k_begin(J, ks + 1); ++kt, ++it) {
@@ -152,8 +167,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     uint32_t it = 0, c = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < P.units && ok && !abort_flag; u += gridDim.x) {
-      const TcJob &J = P.job[find_job(P, u)];
-      const int ks = (u - J.unit_begin) / J.m_tiles;
+      int jb, lu;
+      unit_of(P, u, jb, lu);
+      const TcJob &J = P.job[jb];
+      const int ks = lu / J.m_tiles;
       const int k0 = k_begin(J, ks), k1 = k_begin(J, ks + 1);
       const uint32_t idesc3 = ptx::idesc_bf16_f32(BM, J.xparts * J.Bp);
       const uint32_t idesc2 = ptx::idesc_bf16_f32(BM, 2 * J.Bp);
@@ -202,8 +219,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     uint32_t c = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < P.units && ok; u += gridDim.x) {
-      const TcJob &J = P.job[find_job(P, u)];
-      const int lu = u - J.unit_begin;
+      int jb, lu;
+      unit_of(P, u, jb, lu);
+      const TcJob &J = P.job[jb];
       const int ks = lu / J.m_tiles, mt = lu % J.m_tiles;
       const int k0 = k_begin(J, ks), k1 = k_begin(J, ks + 1);
       const int Bp = J.Bp;
@@ -437,6 +455,11 @@ cudaError_t launch_multi(const JobSpec *jobs, int nj, const MultiPlan &mp, void 
   }
   P.njobs = nj;
   P.units = mp.units;
+  bool same = nj > 1;
+  for (int j = 1; j < nj; ++j)
+    same = same && jobs[j].h == jobs[0].h &&
+           mp.jp[j].m_tiles * mp.jp[j].KS == mp.jp[0].m_tiles * mp.jp[0].KS;
+  P.interleave = same ? 1 : 0;
   P.stages = mp.stages;
   P.chunk = mp.chunk;
   P.stage_bytes = mp.stage_bytes;
@@ -459,18 +482,38 @@ cudaError_t launch_multi(const JobSpec *jobs, int nj, const MultiPlan &mp, void 
 
 }  // namespace
 
+namespace {
+
+// A batch of B scenes against one plan as jobs of at most kMaxBp scenes (at
+// most kMaxJobs of them), run by one interleaved persistent launch.
+int tc_jobs(const psfsim_plan *h, const float *x, int B, float *y, JobSpec *js) {
+  const int64_t cols = psfsim_cols(h);
+  int nj = 0;
+  for (int b0 = 0; b0 < B && nj < kMaxJobs; b0 += kMaxBp, ++nj) {
+    const int c = (B - b0) < kMaxBp ? (B - b0) : kMaxBp;
+    js[nj] = JobSpec{h, x ? x + (int64_t)b0 * cols : nullptr, y ? y + (int64_t)b0 * h->M : nullptr, c, nullptr};
+  }
+  return nj;
+}
+
+constexpr int kMaxLaunchScenes = kMaxJobs * kMaxBp;
+
+}  // namespace
+
 size_t psfsim_forward_tc_scratch(const psfsim_plan *h, int B) {
-  JobSpec js{h, nullptr, nullptr, B < kMaxBp ? B : kMaxBp, nullptr};
-  return plan_multi(&js, 1, nullptr).scratch;
+  JobSpec js[kMaxJobs];
+  const int nj = tc_jobs(h, nullptr, B < kMaxLaunchScenes ? B : kMaxLaunchScenes, nullptr, js);
+  return plan_multi(js, nj, nullptr).scratch;
 }
 
 cudaError_t psfsim_launch_forward_tc(const psfsim_plan *h, const float *x, int B, float *y, void *scratch,
                                      cudaStream_t st) {
-  for (int b0 = 0; b0 < B; b0 += kMaxBp) {
-    const int Bc = (B - b0) < kMaxBp ? (B - b0) : kMaxBp;
-    JobSpec js{h, x + (int64_t)b0 * psfsim_cols(h), y + (int64_t)b0 * h->M, Bc, nullptr};
-    const MultiPlan mp = plan_multi(&js, 1, nullptr);
-    cudaError_t e = launch_multi(&js, 1, mp, scratch, st);
+  for (int b0 = 0; b0 < B; b0 += kMaxLaunchScenes) {
+    const int Bc = (B - b0) < kMaxLaunchScenes ? (B - b0) : kMaxLaunchScenes;
+    JobSpec js[kMaxJobs];
+    const int nj = tc_jobs(h, x + (int64_t)b0 * psfsim_cols(h), Bc, y + (int64_t)b0 * h->M, js);
+    const MultiPlan mp = plan_multi(js, nj, nullptr);
+    cudaError_t e = launch_multi(js, nj, mp, scratch, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
