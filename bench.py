@@ -933,6 +933,13 @@ def _profile_case(name: str) -> None:
         X = torch.from_numpy(workloads.scene_batch(w, 32, kind="two_ring").astype(np.float32)).to(dev)
         for _ in range(2):
             plan.forward(X)
+    elif name == "splitsym128":
+        w = workloads.adjoint_128()
+        plan = Plan(torch.from_numpy(w.library().astype(np.float32)).to(dev), w.radii, w.s, N=w.N, S=w.S,
+                    storage="split_bf16_sym")
+        X = torch.rand(64, w.K, device=dev)
+        for _ in range(3):
+            plan.forward(X)
     elif name in ("tc128", "bf16_128"):
         w = workloads.adjoint_128()
         plan = Plan(torch.from_numpy(w.library().astype(np.float32)).to(dev), w.radii, w.s, N=w.N, S=w.S,
@@ -989,8 +996,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--main-only", action="store_true", help="skip the other workloads' measurements")
     ap.add_argument("--case", default=None,
-                    help="run one small profiling case (fp32_128, fit128, sym128, sparse128, tc128, bf16_128, "
-                         "fused512)")
+                    help="run one small profiling case (fp32_128, fit128, sym128, sparse128, splitsym128, tc128, "
+                         "bf16_128, fused512)")
     args = ap.parse_args()
     if args.case:
         _profile_case(args.case)
