@@ -82,12 +82,14 @@ enum psfsim_interp { PSFSIM_LINEAR = 0, PSFSIM_NEAREST = 1 };
 typedef struct {
   int32_t storage, interp, n, n_r;
   int64_t M, K;
-  int64_t ld;           /* FP32: column stride in floats; SPLIT_BF16, BF16: row stride in elements */
-  int64_t a_offset;     /* FP32: A; SPLIT_BF16, BF16: hi */
-  int64_t lo_offset;    /* SPLIT_BF16: lo (else -1) */
-  int64_t scale_offset; /* SPLIT_BF16, BF16: float32 per-column scale (else -1) */
+  int64_t ld;           /* FP32, FP32_SYM: column stride in floats; SPLIT_BF16, BF16,
+                           SPLIT_BF16_SYM: row stride in elements (K, or K_stored, rounded up to 64) */
+  int64_t a_offset;     /* FP32, FP32_SYM: A; SPLIT_BF16, BF16, SPLIT_BF16_SYM: hi */
+  int64_t lo_offset;    /* SPLIT_BF16, SPLIT_BF16_SYM: lo (else -1) */
+  int64_t scale_offset; /* SPLIT_BF16, BF16, SPLIT_BF16_SYM: float32 per-column scale (else -1) */
   int64_t workspace_bytes;
-  int64_t K_stored;     /* columns held (K; FP32_SYM / FUSED: quadrant columns inside the last radius) */
+  int64_t K_stored;     /* columns held (K; FP32_SYM, SPLIT_BF16_SYM, FUSED: quadrant columns inside
+                           the last radius, in the order of the sorted geometry) */
 } psfsim_info_t;
 
 /* Human-readable name of a status code (static string). */
