@@ -177,56 +177,69 @@ __global__ void __launch_bounds__(kLossThreads) sym_loss_kernel(const float *__r
   }
 }
 
-// gc[m][t] = sum_i A_Q0[i, t] gp[m][i] for t0 <= t < t1, two columns per pass
-// so that each load of the four turned residuals (from L2) serves both: the
-// four rotations would otherwise read four times the bytes of A from L2.
-// Rows split across the CTA (float4 strided), warp sums, then a fixed-order
-// sum over the warps through a double-buffered shared array.
-template <bool kVec>
-__device__ __forceinline__ void adj_pairs(const float *__restrict__ A, int64_t ld, int64_t M, int64_t Kv,
+// gc[m][t] = sum_i A_Q0[i, t] gp[m][i] for t0 <= t < t1, kC columns per pass
+// so that each load of the four turned residuals (from L2) serves all of
+// them (the four rotations would otherwise read four times the bytes of A
+// from L2), with 2 kC column loads in flight per thread.  Rows split across
+// the CTA (float4 strided), warp sums, then a fixed-order sum over the warps
+// through a double-buffered shared array.
+template <bool kVec, int kC>
+__device__ __forceinline__ void adj_group(const float *__restrict__ A, int64_t ld, int64_t M, int64_t Kv,
                                           const float *__restrict__ gp, float *__restrict__ gc, int64_t t0,
                                           int64_t t1) {
-  __shared__ float red[2][kAdjThreads / 32][8];
+  __shared__ float red[2][kAdjThreads / 32][4 * kC];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int parity = 0;
-  for (int64_t t = t0; t < t1; t += 2, parity ^= 1) {
-    const bool two = t + 1 < t1;
-    const float *c0 = A + t * ld;
-    const float *c1 = two ? c0 + ld : c0;
-    float acc[2][4] = {};
+  for (int64_t t = t0; t < t1; t += kC, parity ^= 1) {
+    const int nc = (int)(t1 - t < kC ? t1 - t : kC);
+    const float *col[kC];
+#pragma unroll
+    for (int c = 0; c < kC; ++c) col[c] = A + (t + (c < nc ? c : 0)) * ld;
+    float acc[kC][4] = {};
     if (kVec) {
       const int64_t M4 = M >> 2;
-      auto step = [&](const float4 &v0, const float4 &v1, int64_t i4) {
+      const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+      auto step = [&](const float4 (&v)[kC], int64_t i4) {
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
           const float4 gv = __ldg(reinterpret_cast<const float4 *>(gp + (int64_t)b * M) + i4);
-          acc[0][b] = fmaf(v0.x, gv.x, fmaf(v0.y, gv.y, fmaf(v0.z, gv.z, fmaf(v0.w, gv.w, acc[0][b]))));
-          acc[1][b] = fmaf(v1.x, gv.x, fmaf(v1.y, gv.y, fmaf(v1.z, gv.z, fmaf(v1.w, gv.w, acc[1][b]))));
+#pragma unroll
+          for (int c = 0; c < kC; ++c)
+            acc[c][b] = fmaf(v[c].x, gv.x, fmaf(v[c].y, gv.y, fmaf(v[c].z, gv.z, fmaf(v[c].w, gv.w, acc[c][b]))));
         }
       };
-      const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
       int64_t i4 = threadIdx.x;
-      for (; i4 + kAdjThreads < M4; i4 += 2 * kAdjThreads) {  // four A loads in flight per thread
-        const float4 a0 = ld_stream4(c0 + 4 * i4), b0 = ld_stream4(c0 + 4 * (i4 + kAdjThreads));
-        const float4 a1 = two ? ld_stream4(c1 + 4 * i4) : zero;
-        const float4 b1 = two ? ld_stream4(c1 + 4 * (i4 + kAdjThreads)) : zero;
-        step(a0, a1, i4);
-        step(b0, b1, i4 + kAdjThreads);
+      for (; i4 + kAdjThreads < M4; i4 += 2 * kAdjThreads) {
+        float4 va[kC], vb[kC];
+#pragma unroll
+        for (int c = 0; c < kC; ++c) {
+          va[c] = c < nc ? ld_stream4(col[c] + 4 * i4) : zero;
+          vb[c] = c < nc ? ld_stream4(col[c] + 4 * (i4 + kAdjThreads)) : zero;
+        }
+        step(va, i4);
+        step(vb, i4 + kAdjThreads);
       }
-      for (; i4 < M4; i4 += kAdjThreads) step(ld_stream4(c0 + 4 * i4), two ? ld_stream4(c1 + 4 * i4) : zero, i4);
+      for (; i4 < M4; i4 += kAdjThreads) {
+        float4 va[kC];
+#pragma unroll
+        for (int c = 0; c < kC; ++c) va[c] = c < nc ? ld_stream4(col[c] + 4 * i4) : zero;
+        step(va, i4);
+      }
     } else {
       for (int64_t i = threadIdx.x; i < M; i += kAdjThreads) {
-        const float v0 = __ldg(c0 + i), v1 = two ? __ldg(c1 + i) : 0.f;
+        float v[kC];
+#pragma unroll
+        for (int c = 0; c < kC; ++c) v[c] = c < nc ? __ldg(col[c] + i) : 0.f;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
           const float g = __ldg(gp + (int64_t)b * M + i);
-          acc[0][b] = fmaf(v0, g, acc[0][b]);
-          acc[1][b] = fmaf(v1, g, acc[1][b]);
+#pragma unroll
+          for (int c = 0; c < kC; ++c) acc[c][b] = fmaf(v[c], g, acc[c][b]);
         }
       }
     }
 #pragma unroll
-    for (int c = 0; c < 2; ++c)
+    for (int c = 0; c < kC; ++c)
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         float s = acc[c][b];
@@ -235,7 +248,7 @@ __device__ __forceinline__ void adj_pairs(const float *__restrict__ A, int64_t l
         if (lane == 0) red[parity][warp][c * 4 + b] = s;
       }
     __syncthreads();
-    if (threadIdx.x < (two ? 8 : 4)) {
+    if (threadIdx.x < 4 * nc) {
       const int c = threadIdx.x >> 2, b = threadIdx.x & 3;
       float s = red[parity][0][threadIdx.x];
 #pragma unroll
@@ -256,7 +269,7 @@ struct SymChainArgs {
 };
 
 // CTA c: compact columns [Kv c / G, Kv (c+1) / G).  gc[m][t] = (A_Q0^T gp_m)_t
-// (adj_pairs); then gz at the four turned pixels of each column and the
+// (adj_group, three columns per pass); then gz at the four turned pixels of each column and the
 // FP64 chain partial sum_{t,m} gc[m][t] dZ/dtheta at that pixel (fixed thread
 // assignment, fixed tree); pixels whose quadrant column lies beyond the last
 // radius get gz = 0 (disjoint from the pixels the columns write).
@@ -269,7 +282,7 @@ __global__ void __launch_bounds__(kAdjThreads, 4)
   ptx::griddep_launch_dependents();
   ptx::griddep_wait();  // gp and dZ/dtheta come from the earlier kernels
   const int64_t t0 = Kv * blockIdx.x / gridDim.x, t1 = Kv * (blockIdx.x + 1) / gridDim.x;
-  adj_pairs<kVec>(A, ld, M, Kv, gp, gc, t0, t1);
+  adj_group<kVec, 3>(A, ld, M, Kv, gp, gc, t0, t1);
   __syncthreads();  // this CTA's gc entries are written
   const int64_t K = (int64_t)N * N;
   double acc[5] = {0, 0, 0, 0, 0};
