@@ -38,7 +38,7 @@ METRIC = "simulated images/s and GMAC/s (fraction of HBM/tensor roofline) vs pla
 NCU_TRAFFIC = {
     "forward": 1.073864e9 + 0.003710e9,        # fwd_ring_loss_kernel, 128^2
     "adjoint": 1.074212e9 + 0.005124e9,        # adj_chain_kernel, 128^2
-    "tc_gemm_per_A_byte": (1.086450e9 + 0.028076e9) / (16384 * 16384 * 4),
+    "tc_gemm_per_A_byte": (1.086379e9 + 0.026419e9) / (16384 * 16384 * 4),
     "fused": 1.991590e9 + 0.127414e9,          # fused_kernel (two rows per lane), 512^2, 32 scenes
 }
 
