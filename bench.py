@@ -34,7 +34,7 @@ METRIC = "simulated images/s and GMAC/s (fraction of HBM/tensor roofline) vs pla
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the current kernels (profiles/*.md).  The tensor-core figure is
-# from the 128^2 case and scales with the bytes of A (traffic / A = 1.0375 there).
+# from the 128^2 case and scales with the bytes of A (traffic / A = 1.0364 there).
 NCU_TRAFFIC = {
     "forward": 1.073864e9 + 0.003710e9,        # fwd_ring_loss_kernel, 128^2
     "adjoint": 1.074212e9 + 0.005124e9,        # adj_chain_kernel, 128^2
