@@ -33,8 +33,11 @@ constexpr int BM = 128;
 constexpr int BK = 64;
 constexpr int kMaxStages = 8;
 constexpr int kThreads = 192;
-constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kAccStride = 256;  // TMEM column offset of the second accumulator
+// TMEM per CTA: two accumulators of up to 256 columns (one CTA per SM), or,
+// when every accumulator fits in 128 columns (BF16 storage, 64 scenes or
+// fewer), two of 128 so that two CTAs, two load/MMA pipelines, share an SM.
+constexpr uint32_t kTmemColsWide = 512, kAccStrideWide = 256;
+constexpr uint32_t kTmemColsNarrow = 256, kAccStrideNarrow = 128;
 constexpr uint32_t kTileBytes = BM * BK * 2;
 constexpr int kMaxBp = 80;       // 3 * Bp <= 256 (MMA N and TMA box limits), Bp % 16 == 0
 constexpr int kMaxJobs = 16;
@@ -61,6 +64,7 @@ struct TcMulti {
   uint32_t stage_bytes;
   uint32_t x_off;  // byte offset of the x tile in a stage: after hi and lo, or after hi alone
   int interleave;  // jobs share one A and one unit count: unit u is job u % njobs, unit u / njobs
+  uint32_t tmem_cols, acc_stride;
   int *status;
 };
 
@@ -109,7 +113,7 @@ __device__ __forceinline__ void unit_of(const TcMulti &P, int u, int &jb, int &l
 
 __device__ __forceinline__ int k_begin(const TcJob &J, int ks) { return (int)((int64_t)J.k_tiles * ks / J.KS); }
 
-__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcMulti P) {
+__global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_constant__ TcMulti P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], tfull_bar[2], tempty_bar[2];
@@ -130,7 +134,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     ptx::fence_mbar_init();
   }
   if (warp == 0) {
-    ptx::tmem_alloc(&tmem_base_sh, kTmemCols);
+    ptx::tmem_alloc(&tmem_base_sh, P.tmem_cols);
     ptx::tmem_relinquish();
   }
   ptx::tc_fence_before();
@@ -184,7 +188,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           break;
         }
         ptx::tc_fence_after();
-        const uint32_t d_tmem = tbase + acc * kAccStride;
+        const uint32_t d_tmem = tbase + acc * P.acc_stride;
         for (int kt = kc; kt < kc1; ++kt, ++it) {
           const int s = (int)(it % P.stages);
           if (!ptx::mbar_wait_bounded(&full_bar[s], (it / P.stages) & 1)) {
@@ -246,7 +250,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         // Already complete (lane 0 saw it): this gives every lane its acquire.
         if (!ptx::mbar_wait_bounded(&tfull_bar[acc], (c >> 1) & 1)) set_abort(&abort_flag, P.status);
         ptx::tc_fence_after();
-        const uint32_t tacc = tbase + ((uint32_t)(quarter * 32) << 16) + acc * kAccStride;
+        const uint32_t tacc = tbase + ((uint32_t)(quarter * 32) << 16) + acc * P.acc_stride;
 #pragma unroll
         for (int q = 0; q < kMaxBp / 16; ++q) {
           if (q * 16 < Bp) {
@@ -280,7 +284,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   if (warp == 0) {
     __syncwarp();
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tbase, kTmemCols);
+    ptx::tmem_dealloc(tbase, P.tmem_cols);
   }
 }
 
@@ -345,8 +349,8 @@ struct JobPlan {
 
 struct MultiPlan {
   JobPlan jp[kMaxJobs];
-  int njobs, units, stages, chunk;
-  uint32_t stage_bytes, x_off;
+  int njobs, units, stages, chunk, ctas_per_sm;
+  uint32_t stage_bytes, x_off, tmem_cols, acc_stride;
   size_t smem, scratch;
 };
 
@@ -407,7 +411,13 @@ MultiPlan plan_multi(const JobSpec *jobs, int nj, const psfsim_tuning_t *tune) {
   }
   mp.x_off = (any_lo ? 2 : 1) * kTileBytes;
   mp.stage_bytes = (uint32_t)psfsim_round_up(mp.x_off + (int64_t)x_rows * BK * 2, 1024);
-  int fit = (int)((220 * 1024) / mp.stage_bytes);
+  // Accumulators of at most 128 columns: two CTAs per SM, each with half the
+  // shared memory and half the tensor memory.
+  const bool narrow = x_rows <= (int)kAccStrideNarrow;
+  mp.ctas_per_sm = narrow ? 2 : 1;
+  mp.tmem_cols = narrow ? kTmemColsNarrow : kTmemColsWide;
+  mp.acc_stride = narrow ? kAccStrideNarrow : kAccStrideWide;
+  int fit = (int)(((narrow ? 108 : 220) * 1024) / mp.stage_bytes);
   fit = fit > kMaxStages ? kMaxStages : fit;
   mp.stages = tune && tune->stages >= 2 && tune->stages < fit ? tune->stages : fit;
   // A k-tile is 4 MMAs per accumulator (8 with lo), so at most 16 (8) k-tiles
@@ -460,6 +470,8 @@ cudaError_t launch_multi(const JobSpec *jobs, int nj, const MultiPlan &mp, void 
     same = same && jobs[j].h == jobs[0].h &&
            mp.jp[j].m_tiles * mp.jp[j].KS == mp.jp[0].m_tiles * mp.jp[0].KS;
   P.interleave = same ? 1 : 0;
+  P.tmem_cols = mp.tmem_cols;
+  P.acc_stride = mp.acc_stride;
   P.stages = mp.stages;
   P.chunk = mp.chunk;
   P.stage_bytes = mp.stage_bytes;
@@ -469,7 +481,8 @@ cudaError_t launch_multi(const JobSpec *jobs, int nj, const MultiPlan &mp, void 
       cudaSuccess)
     return e;
   const int num_sms = jobs[0].h->num_sms;
-  tc_gemm_kernel<<<mp.units < num_sms ? mp.units : num_sms, kThreads, mp.smem, st>>>(P);
+  const int slots = num_sms * mp.ctas_per_sm;
+  tc_gemm_kernel<<<mp.units < slots ? mp.units : slots, kThreads, mp.smem, st>>>(P);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int j = 0; j < nj; ++j) {
     const JobPlan &p = mp.jp[j];
