@@ -39,7 +39,7 @@ NCU_TRAFFIC = {
     "forward": 1.073864e9 + 0.003710e9,        # fwd_ring_loss_kernel, 128^2
     "adjoint": 1.074212e9 + 0.005124e9,        # adj_chain_kernel, 128^2
     "tc_gemm_per_A_byte": (1.086379e9 + 0.026419e9) / (16384 * 16384 * 4),
-    "fused": 1.991590e9 + 0.127414e9,          # fused_kernel (two rows per lane), 512^2, 32 scenes
+    "fused": 2.031170e9 + 0.127913e9,          # fused_kernel, 512^2, 32 scenes
 }
 
 
@@ -642,7 +642,7 @@ def _path_fused(dev, stream, with_oracle):
     c = (np.arange(w.N // 2) + 0.5) * w.S
     q0 = np.hypot(c[:, None], c[None, :]) <= w.radii[-1]
     elems = int(q0.sum()) * w.M
-    inst_per_elem = 91.7  # ncu: thread instructions per generated element (profiles/fused_kernel_512.md)
+    inst_per_elem = 87.1  # ncu: thread instructions per generated element (profiles/fused_kernel_512.md)
     peak_inst = props.multi_processor_count * 4 * 32 * 2.07e9
     achieved_inst = elems * inst_per_elem / (ms / 1e3)
     out = {"workload": "fused_512: 80 PSFs 512^2 at 0.0625 lambda/D, A 262144^2 never stored, 32 two-ring scenes",

@@ -67,7 +67,7 @@ struct ColEntry {
   long long A0, B0;
   uint32_t Clo, Slo, NSlo;
   int32_t Chi, Shi, NShi;
-  int64_t off;  // offset of L[k] in the quad-layout library, or -1 for padding columns
+  int64_t off;  // offset of L[k] in the quad-layout library (0 for padding columns)
   float w0, w1;
 };
 
@@ -82,13 +82,15 @@ __device__ __forceinline__ void split64(long long v, uint32_t &lo, int32_t &hi) 
   hi = (int32_t)(v >> 32);
 }
 
-// The two bilinear weights of one axis from the 32-bit fixed-point fraction:
-// the smaller one is converted (relative accuracy 2^-24), the larger one is
-// 1 - smaller, exact because the smaller is at most 1/2.
+// The two bilinear weights of one axis from the 32-bit fixed-point fraction,
+// in units of 2^-32: the smaller one is converted (relative accuracy 2^-24),
+// the larger one is 2^32 - smaller, exact because the smaller is at most 2^31.
+// The two factors 2^-32 are applied as exact power-of-two scalings elsewhere:
+// one in the column weights w0, w1 of the table, one in the epilogue.
 __device__ __forceinline__ void axis_weights(unsigned f, float &w_lo_tap, float &w_hi_tap) {
   const bool low = f <= 0x80000000u;
-  const float small = __uint2float_rn(low ? f : 0u - f) * 2.3283064365386963e-10f;
-  const float large = 1.f - small;
+  const float small = __uint2float_rn(low ? f : 0u - f);
+  const float large = 4294967296.f - small;
   w_hi_tap = low ? small : large;
   w_lo_tap = low ? large : small;
 }
@@ -138,15 +140,17 @@ __global__ void fused_xgather(const float *__restrict__ x, int B, int Bp, int N,
   }
 }
 
-// One A element from a column-table entry and the pixel's fixed-point source
-// coordinates (a2, b2).  The 2 x 2 footprint of each PSF is one float4 of the
-// quad-layout library, so only the footprint position needs a check.
+// One A element, times 2^32, from a column-table entry and the pixel's
+// fixed-point source coordinates (a2, b2).  The 2 x 2 footprint of each PSF
+// is one float4 of the quad-layout library, so only the footprint position
+// (q0, p0 in [-1, n-1]) needs a check.  Padding columns have weights 0 and an
+// in-range footprint, so they give 0 without a test of their own.
 __device__ __forceinline__ float gen_element(const ColEntry &e, const float4 *__restrict__ qlib, int n,
                                              int64_t qsz, long long a2, long long b2) {
   constexpr int kShift = PSFSIM_FRAC_BITS + 1;
   const int q0 = (int)(a2 >> kShift);
   const int p0 = (int)(b2 >> kShift);
-  if (e.off < 0 || q0 < -1 || q0 > n - 1 || p0 < -1 || p0 > n - 1) return 0.f;
+  if ((unsigned)(q0 + 1) > (unsigned)n || (unsigned)(p0 + 1) > (unsigned)n) return 0.f;
   float wa0, wa1, wb0, wb1;
   axis_weights((unsigned)((unsigned long long)a2 >> (kShift - 32)), wa0, wa1);
   axis_weights((unsigned)((unsigned long long)b2 >> (kShift - 32)), wb0, wb1);
@@ -361,9 +365,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             ColEntry *tab = ctab[tg & 1];
             for (int c = gtid; c < kTabTiles * BK; c += kGenWarps * 32) {
               const int64_t t = (int64_t)kt * BK + c;
-              ColEntry e;
-              e.off = -1;
-              e.A0 = e.B0 = 0;
+              ColEntry e;  // padding: zero steps from the centre pixel, zero weights
+              e.off = 0;
+              e.A0 = e.B0 = base;
               e.Clo = e.Slo = e.NSlo = 0;
               e.Chi = e.Shi = e.NShi = 0;
               e.w0 = e.w1 = 0.f;
@@ -375,8 +379,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 split64(gm.Sn, e.Slo, e.Shi);
                 split64(-gm.Sn, e.NSlo, e.NShi);
                 e.off = (int64_t)gm.k * P.psz;
-                e.w0 = gm.w0;
-                e.w1 = gm.w1;
+                e.w0 = gm.w0 * 0x1p-32f;
+                e.w1 = gm.w1 * 0x1p-32f;
               }
               tab[c] = e;
             }
@@ -448,7 +452,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         float *out = P.part + ((int64_t)(ks * 4 + rot) * P.B) * P.rows + (int64_t)pp * n + qp;
 #pragma unroll
         for (int t = 0; t < kMaxBp; ++t)
-          if (t < P.B) out[(int64_t)t * P.rows] = sum[t];
+          if (t < P.B) out[(int64_t)t * P.rows] = sum[t] * 0x1p-32f;
       }
     }
   }
