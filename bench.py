@@ -770,6 +770,19 @@ def _path_sym(dev, stream, hbm):
     torch.cuda.synchronize()
     fwd_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
     adj_ms = float(np.mean([e[2].elapsed_time(e[3]) for e in ev]))
+    # A_Q0 (0.12 GB) fits in L2, so back-to-back steps can find some of it there; also time
+    # single steps with L2 flushed before each (a 512 MB buffer rewritten between steps).
+    flush = torch.empty(512 * 2**20 // 4, dtype=torch.float32, device=dev)
+    nf = 200
+    evf = [_events(2) for _ in range(nf)]
+    for i in range(nf):
+        flush.add_(1.0)
+        evf[i][0].record(stream)
+        ps.enqueue_gradient(theta)
+        evf[i][1].record(stream)
+    torch.cuda.synchronize()
+    flushed_ms = float(np.median([e[0].elapsed_time(e[1]) for e in evf]))
+    del flush
     kst = sym.info.K_stored
     stored = 4 * sym.info.ld * kst
     dom = "adjoint" if adj_ms > fwd_ms else "forward"
@@ -779,6 +792,8 @@ def _path_sym(dev, stream, hbm):
                         f"inside 12 lambda/D are stored ({kst} of {w.K} columns, {stored / 1e9:.3f} GB); "
                         "three launches per gradient",
             "images_per_s": 1e3 / ms, "ms_per_step": ms,
+            "l2": "back to back (A_Q0 is smaller than L2); flushed_l2 below rewrites 512 MB before each step",
+            "flushed_l2": {"images_per_s": 1e3 / flushed_ms, "ms_per_step_median": flushed_ms},
             "kernels_ms": {"forward_half": fwd_ms, "adjoint_half": adj_ms},
             "roofline": {"bound": "hbm", "achieved": nbytes / (dom_ms / 1e3) / 1e9,
                          "peak": hbm, "unit": "GB/s", "frac": nbytes / (dom_ms / 1e3) / 1e9 / hbm,

@@ -68,10 +68,16 @@ __global__ void __cluster_dims__(1, kCluster, 1) __launch_bounds__(kFwdThreads, 
   const int64_t tile0 = (int64_t)blockIdx.x * kRowsPerCta;
   ptx::griddep_launch_dependents();
   // Until griddep_wait: no global writes, no reads of earlier kernels' results.
-  for (int64_t t = t0 + threadIdx.x; t < t1; t += kFwdThreads) {
-    const int j0 = __ldg(order + t);
-#pragma unroll
-    for (int m = 0; m < 4; ++m) xs[m * kXCols + (t - t0)] = ring_eval<false>(P, turned_pixel(P.N, j0, m), nullptr);
+  {  // the first columns' rows head for L2 while the scene values are computed
+    const int64_t r = tile0 + 4 * threadIdx.x;
+    if (r < ld)
+      for (int64_t t = t0; t < t0 + 4 && t < t1; ++t)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(A + t * ld + r));
+  }
+  for (int64_t u = threadIdx.x; u < 4 * (t1 - t0); u += kFwdThreads) {
+    const int64_t t = t0 + (u >> 2);
+    const int m = (int)(u & 3);
+    xs[m * kXCols + (t - t0)] = ring_eval<false>(P, turned_pixel(P.N, __ldg(order + t), m), nullptr);
   }
   __syncthreads();
   {
@@ -111,24 +117,32 @@ __global__ void __cluster_dims__(1, kCluster, 1) __launch_bounds__(kFwdThreads, 
     }
   }
   ptx::cluster_sync();  // every rank has read the others' shared memory
-  if (threadIdx.x >= kSliceVec) return;
   __shared__ unsigned last;
   __threadfence();
-  ptx::named_barrier_sync(1, kSliceVec);
+  __syncthreads();
   const unsigned slot = blockIdx.x * kCluster + q;
   if (threadIdx.x == 0) last = atomicAdd(slice_count + slot, 1u) == (unsigned)(G - 1);
-  ptx::named_barrier_sync(1, kSliceVec);
+  __syncthreads();
   if (!last) return;
   __threadfence();
-  if (rs < ld) {
+  {  // the last group of the slice: thread (m, i) sums rotation m of row quad i over the groups
+    const int m = (int)threadIdx.x / kSliceVec;
+    const int64_t r2 = tile0 + 4 * ((int64_t)q * kSliceVec + (int)threadIdx.x % kSliceVec);
+    if (r2 < ld) {
+      const float4 *src = reinterpret_cast<const float4 *>(part + (int64_t)m * ld + r2);  // group g at src + g ld
+      float4 t = __ldcg(src);
+      for (int g0 = 1; g0 < G; g0 += 4) {  // four loads in flight, added in ascending g
+        float4 u[4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      float4 t = __ldcg(reinterpret_cast<const float4 *>(part + (int64_t)m * ld + rs));
-      for (int g = 1; g < G; ++g) {
-        const float4 u = __ldcg(reinterpret_cast<const float4 *>(part + ((int64_t)g * 4 + m) * ld + rs));
-        t.x += u.x; t.y += u.y; t.z += u.z; t.w += u.w;
+        for (int e = 0; e < 4; ++e)
+          if (g0 + e < G) u[e] = __ldcg(src + (int64_t)(g0 + e) * ld);
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (g0 + e < G) {
+            t.x += u[e].x; t.y += u[e].y; t.z += u[e].z; t.w += u[e].w;
+          }
       }
-      *reinterpret_cast<float4 *>(v + (int64_t)m * ld + rs) = t;
+      *reinterpret_cast<float4 *>(v + (int64_t)m * ld + r2) = t;
     }
   }
   if (threadIdx.x == 0) slice_count[slot] = 0u;
@@ -269,35 +283,32 @@ struct SymChainArgs {
 };
 
 // CTA c: compact columns [Kv c / G, Kv (c+1) / G).  gc[m][t] = (A_Q0^T gp_m)_t
-// (adj_group, three columns per pass); then gz at the four turned pixels of each column and the
-// FP64 chain partial sum_{t,m} gc[m][t] dZ/dtheta at that pixel (fixed thread
-// assignment, fixed tree); pixels whose quadrant column lies beyond the last
-// radius get gz = 0 (disjoint from the pixels the columns write).
+// (adj_group, four columns per pass, eight column loads in flight per thread,
+// three CTAs per SM so that nothing spills); pixels whose quadrant column lies
+// beyond the last radius get gz = 0 (all threads; disjoint from the pixels
+// the columns write); then warp 0 alone writes gz at the four turned pixels
+// of each column and forms the FP64 chain partial sum_{t,m} gc[m][t] dZ/dtheta
+// at that pixel (lane-strided, fixed butterfly): FP64 runs at a small fraction
+// of the FP32 rate, so the other warps take no part in it.
 template <bool kVec>
-__global__ void __launch_bounds__(kAdjThreads, 4)
+__global__ void __launch_bounds__(kAdjThreads, 3)
     adj_sym_chain_kernel(const float *__restrict__ A, int64_t ld, int64_t M, int64_t Kv, const int *__restrict__ order,
                          const ColGeom *__restrict__ geom, int N, const float *__restrict__ gp,
                          float *__restrict__ gc, float *__restrict__ gz, const SymChainArgs c) {
-  __shared__ double red[kAdjThreads / 32][5];
   ptx::griddep_launch_dependents();
   ptx::griddep_wait();  // gp and dZ/dtheta come from the earlier kernels
   const int64_t t0 = Kv * blockIdx.x / gridDim.x, t1 = Kv * (blockIdx.x + 1) / gridDim.x;
-  adj_group<kVec, 3>(A, ld, M, Kv, gp, gc, t0, t1);
+  adj_group<kVec, 4>(A, ld, M, Kv, gp, gc, t0, t1);
   __syncthreads();  // this CTA's gc entries are written
+  // The grid shape again, from fresh special-register reads, so that the
+  // streaming loop above keeps no extra registers live for this tail.
+  unsigned cta, ncta;
+  asm volatile("mov.u32 %0, %%ctaid.x;" : "=r"(cta));
+  asm volatile("mov.u32 %0, %%nctaid.x;" : "=r"(ncta));
   const int64_t K = (int64_t)N * N;
-  double acc[5] = {0, 0, 0, 0, 0};
-  for (int64_t u = threadIdx.x; u < 4 * (t1 - t0); u += kAdjThreads) {
-    const int64_t t = t0 + u / 4;
-    const int m = (int)(u % 4);
-    const int64_t p = turned_pixel(N, __ldg(order + t), m);
-    const float val = gc[(int64_t)m * Kv + t];
-    gz[p] = val;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) acc[k] += (double)val * (double)__ldg(c.jac + k * K + p);
-  }
   {  // pixels without a column
     const int H = N / 2;
-    for (int64_t p = (int64_t)blockIdx.x * kAdjThreads + threadIdx.x; p < K; p += (int64_t)gridDim.x * kAdjThreads) {
+    for (int64_t p = (int64_t)cta * kAdjThreads + threadIdx.x; p < K; p += (int64_t)ncta * kAdjThreads) {
       int ix = (int)(p % N), iy = (int)(p / N);
       for (int k = 0; k < 3 && !(ix >= H && iy >= H); ++k) {  // R^-1(ix, iy) = (iy, N-1-ix)
         const int nx = iy;
@@ -307,26 +318,31 @@ __global__ void __launch_bounds__(kAdjThreads, 4)
       if (geom[(int64_t)(iy - H) * H + (ix - H)].k < 0) gz[p] = 0.f;
     }
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x >= 32) return;
+  // Warp 0: gz at the four turned pixels of each of the CTA's columns, and the
+  // FP64 chain partial (lane-strided entries, then a fixed butterfly).
+  const int lane = threadIdx.x;
+  const int64_t c0 = Kv * cta / ncta, c1 = Kv * (cta + 1) / ncta;
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int64_t u = lane; u < 4 * (c1 - c0); u += 32) {
+    const int64_t t = c0 + u / 4;
+    const int m = (int)(u % 4);
+    const int64_t p = turned_pixel(N, __ldg(order + t), m);
+    const float val = gc[(int64_t)m * Kv + t];
+    gz[p] = val;
 #pragma unroll
-  for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < 5; ++k) acc[k] += (double)val * (double)__ldg(c.jac + k * K + p);
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-    if (lane == 0) red[warp][k] = acc[k];
-  }
-  __syncthreads();
-  if (warp != 0) return;
-  const unsigned cta = blockIdx.x, ncta = gridDim.x;
   const unsigned grp = cta / kGroup, ngrp = (ncta + kGroup - 1) / kGroup;
   const unsigned gsize = ncta - grp * kGroup < kGroup ? ncta - grp * kGroup : kGroup;
   unsigned last = 0;
   if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      double s = red[0][k];
-      for (int w = 1; w < kAdjThreads / 32; ++w) s += red[w][k];
-      c.chain_part[cta * 5 + k] = s;
-    }
+    for (int k = 0; k < 5; ++k) c.chain_part[cta * 5 + k] = acc[k];
     __threadfence();
     last = atomicAdd(c.count + grp, 1u) == gsize - 1;
   }
