@@ -137,6 +137,72 @@ __global__ void __cluster_dims__(1, kFwdCluster, 1) __launch_bounds__(kFwdThread
 
 constexpr int kChainGroup = 32;  // CTAs whose chain partials one group sum covers
 
+
+// gz[j] = sum_i A[i, j] g[i] for j0 <= j < j1, two columns per pass: one
+// block barrier per pair of columns (the barrier after every column left the
+// stream with nothing in flight once per column) and each residual load
+// serves both.  Per column each thread adds its rows in ascending order
+// (strides of the block), then a fixed butterfly and a fixed sum over the
+// warps; stash[j - j0] = gz[j] for the first kStashCols columns.
+template <bool kVec>
+__device__ __forceinline__ void adj_pairs(const float *__restrict__ A, int64_t ld, int64_t M, int64_t K,
+                                          const float *__restrict__ g, float *__restrict__ gx, int64_t j0,
+                                          int64_t j1, float *stash) {
+  __shared__ float red2[2][kAdjThreads / 32][2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int parity = 0;
+  for (int64_t j = j0; j < j1; j += 2, parity ^= 1) {
+    const bool two = j + 1 < j1;
+    const float *c0 = A + j * ld;
+    const float *c1 = two ? c0 + ld : c0;
+    float a0 = 0.f, a1 = 0.f;
+    if (kVec) {
+      const int64_t M4 = M >> 2;
+      constexpr int T = kAdjThreads;
+      int64_t i4 = threadIdx.x;
+      for (; i4 + T < M4; i4 += 2 * T) {
+        const float4 u0 = ld_stream4(c0 + 4 * i4), w0 = ld_stream4(c1 + 4 * i4);
+        const float4 u1 = ld_stream4(c0 + 4 * (i4 + T)), w1 = ld_stream4(c1 + 4 * (i4 + T));
+        const float4 g0 = __ldg(reinterpret_cast<const float4 *>(g) + i4);
+        const float4 g1 = __ldg(reinterpret_cast<const float4 *>(g) + i4 + T);
+        a0 = fmaf(u0.x, g0.x, a0); a0 = fmaf(u0.y, g0.y, a0); a0 = fmaf(u0.z, g0.z, a0); a0 = fmaf(u0.w, g0.w, a0);
+        a1 = fmaf(w0.x, g0.x, a1); a1 = fmaf(w0.y, g0.y, a1); a1 = fmaf(w0.z, g0.z, a1); a1 = fmaf(w0.w, g0.w, a1);
+        a0 = fmaf(u1.x, g1.x, a0); a0 = fmaf(u1.y, g1.y, a0); a0 = fmaf(u1.z, g1.z, a0); a0 = fmaf(u1.w, g1.w, a0);
+        a1 = fmaf(w1.x, g1.x, a1); a1 = fmaf(w1.y, g1.y, a1); a1 = fmaf(w1.z, g1.z, a1); a1 = fmaf(w1.w, g1.w, a1);
+      }
+      for (; i4 < M4; i4 += T) {
+        const float4 u0 = ld_stream4(c0 + 4 * i4), w0 = ld_stream4(c1 + 4 * i4);
+        const float4 g0 = __ldg(reinterpret_cast<const float4 *>(g) + i4);
+        a0 = fmaf(u0.x, g0.x, a0); a0 = fmaf(u0.y, g0.y, a0); a0 = fmaf(u0.z, g0.z, a0); a0 = fmaf(u0.w, g0.w, a0);
+        a1 = fmaf(w0.x, g0.x, a1); a1 = fmaf(w0.y, g0.y, a1); a1 = fmaf(w0.z, g0.z, a1); a1 = fmaf(w0.w, g0.w, a1);
+      }
+    } else {
+      for (int64_t i = threadIdx.x; i < M; i += kAdjThreads) {
+        const float gi = __ldg(g + i);
+        a0 = fmaf(__ldg(c0 + i), gi, a0);
+        a1 = fmaf(__ldg(c1 + i), gi, a1);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    }
+    if (lane == 0) {
+      red2[parity][warp][0] = a0;
+      red2[parity][warp][1] = a1;
+    }
+    __syncthreads();
+    if (threadIdx.x < (two ? 2 : 1)) {
+      float t = red2[parity][0][threadIdx.x];
+#pragma unroll
+      for (int w = 1; w < kAdjThreads / 32; ++w) t += red2[parity][w][threadIdx.x];
+      gx[j + threadIdx.x] = t;
+      if (j + threadIdx.x - j0 < kStashCols) stash[j + threadIdx.x - j0] = t;
+    }
+  }
+}
+
 struct ChainArgs {
   const float *jac;         // dZ_j/dtheta_m at jac[m * K + j]
   double *chain_part;       // [gridDim.x][5]
@@ -147,14 +213,15 @@ struct ChainArgs {
   double *out;              // {L, dL/dtheta_0..4}
 };
 
-// gz = A^T g over the CTA's contiguous column range (as adj_kernel<1, kVec>),
-// then warp 0 dots the range's gz with dZ/dtheta (both in shared memory: gz
+// gz = A^T g over the CTA's contiguous column range (adj_pairs: two columns
+// per pass, four CTAs of 64 registers per SM so that the stream loop does not
+// spill), then warp 0 dots the range's gz with dZ/dtheta (both in shared memory: gz
 // stashed as it is produced, the Jacobian copied by cp.async while A
 // streams).  Partials are added in two levels, each by the last warp to
 // arrive: the 32 CTAs of a group in CTA order, then the groups in group order
 // together with the loss partials; the butterfly shuffles are a fixed tree.
 template <bool kVec>
-__global__ void __launch_bounds__(kAdjThreads, 6)
+__global__ void __launch_bounds__(kAdjThreads, 4)
     adj_chain_kernel(const float *__restrict__ A, int64_t ld, int64_t M, int64_t K, const float *__restrict__ g,
                      float *__restrict__ gz, const ChainArgs c) {
   __shared__ float gzs[kStashCols];
@@ -172,7 +239,7 @@ __global__ void __launch_bounds__(kAdjThreads, 6)
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   }
-  adj_columns<1, kVec>(A, ld, M, K, g, 0, gz, K * blockIdx.x / gridDim.x, K * (blockIdx.x + 1) / gridDim.x, gzs);
+  adj_pairs<kVec>(A, ld, M, K, g, gz, K * blockIdx.x / gridDim.x, K * (blockIdx.x + 1) / gridDim.x, gzs);
   asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();  // gzs (thread 0) and every thread's Jacobian copies are complete
   if (threadIdx.x >= 32) return;
