@@ -38,7 +38,7 @@ METRIC = "simulated images/s and GMAC/s (fraction of HBM/tensor roofline) vs pla
 NCU_TRAFFIC = {
     "forward": 1.073864e9 + 0.003710e9,        # fwd_ring_loss_kernel, 128^2
     "adjoint": 1.074243e9 + 0.003091e9,        # adj_chain_kernel (two columns per pass), 128^2
-    "tc_gemm_per_A_byte": (1.086379e9 + 0.026419e9) / (16384 * 16384 * 4),
+    "tc_gemm_per_A_byte": (1.086396e9 + 0.026477e9) / (16384 * 16384 * 4),
     "fused": 2.031170e9 + 0.127913e9,          # fused_kernel, 512^2, 32 scenes
 }
 
