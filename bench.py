@@ -529,29 +529,6 @@ def _path_bf16(dev, stream, hbm, with_oracle):
     return out
 
 
-def convolution_image(scene, col_ref, iy_ref: int, ix_ref: int, mask_radius_px=None):
-    """Convolution comparator (Sec. 3): the scene (N x N) convolved with one PSF, the method's
-    column of scene pixel (iy_ref, ix_ref) re-centred on its core, optionally masked to a disk of
-    mask_radius_px pixels around the core; linear convolution by zero-padded FFTs (cuFFT through
-    torch.fft) on the n x n image grid.  Needs s = S and n - N even (the scene grid then maps
-    onto the image grid by an integer offset)."""
-    import torch
-    n, N = col_ref.shape[0], scene.shape[0]
-    o = (n - N) // 2                                  # image pixel of scene pixel (0, 0)
-    cp, cq = iy_ref + o, ix_ref + o                   # the reference column's core pixel
-    g = col_ref
-    if mask_radius_px is not None:
-        pp = torch.arange(n, device=g.device).view(-1, 1)
-        qq = torch.arange(n, device=g.device).view(1, -1)
-        g = torch.where((pp - cp) ** 2 + (qq - cq) ** 2 <= mask_radius_px ** 2, g, torch.zeros_like(g))
-    P = 2 * n
-    xp = torch.zeros(P, P, device=g.device, dtype=torch.float32)
-    xp[o:o + N, o:o + N] = scene
-    kp = torch.roll(torch.nn.functional.pad(g, (0, P - n, 0, P - n)), shifts=(-cp, -cq), dims=(0, 1))
-    out = torch.fft.irfft2(torch.fft.rfft2(xp) * torch.fft.rfft2(kp), s=(P, P))
-    return out[:n, :n]
-
-
 def _path_convolution(dev, stream):
     """Sec. 3's comparison: the fit workload's exozodi ring simulated by the method and by
     convolution with the method's own PSF at 6 lambda/D (+x axis), masked to its core
@@ -559,6 +536,7 @@ def _path_convolution(dev, stream):
     for the scene as is and with its core (r < 3 lambda/D) masked."""
     import torch
     from paper_2106_09122_gb300 import Plan
+    from paper_2106_09122_gb300.convolution import convolution_image
     from synth import workloads
     w = workloads.adjoint_128()
     plan = Plan(torch.from_numpy(w.library().astype(np.float32)).to(dev), w.radii, w.s, N=w.N, S=w.S)
@@ -675,11 +653,8 @@ def _path_uneven(dev, stream, hbm, with_oracle):
     lib = torch.from_numpy(lib32).to(dev)
     buckets = workloads.uneven_buckets()
     plans = {k: Plan(lib, w.radii, w.s, N=k[0], S=k[1], storage="split_bf16") for k in buckets}
-    rng = np.random.default_rng(w.seed + 9)
-    order = [buckets[i] for i in rng.integers(0, len(buckets), 500)]
     W = 50
-    waves = [order[i:i + W] for i in range(0, len(order), W)]
-    cap = max(max(wv.count(k) for k in buckets) for wv in waves)
+    order, waves, cap = workloads.uneven_arrivals(500, W, w.seed + 9)
     server = UnevenServer(plans, capacity=cap)
     mf = server.mf
     for j, k in enumerate(server.keys):

@@ -194,14 +194,20 @@ int psfsim_forward_multi(const psfsim_job_t *jobs, int njobs, const psfsim_tunin
  * paper has no counterpart; this is a deployment convenience.
  *   Same arguments and result as psfsim_forward (FP32 storage only), but the
  *   partial sums live in a PSFSIM_STATIC_SCRATCH_BYTES array compiled into
- *   the library; every GPU that loads the library holds it until exit.
- *   Nothing is allocated: no cudaMalloc, no cudaFree, no allocating library call.
+ *   the library.  The driver reserves that array on a device when it loads
+ *   the library's device code there -- with CUDA's default lazy loading, at
+ *   the first psfsim_forward_static call on that device, so 16 MiB of device
+ *   memory must be free at that moment -- and the device holds it until the
+ *   process exits.  The call itself allocates nothing: no cudaMalloc, no
+ *   cudaFree, no allocating library call.
  *   Returns PSFSIM_ERR_WORKSPACE when this plan's partial sums for B scenes
  *   (psfsim_forward_scratch_bytes(h, B)) exceed PSFSIM_STATIC_SCRATCH_BYTES,
  *   PSFSIM_ERR_ARG when the current device is not the plan's device.
  *   The first call on a device looks up the array's device address (a
- *   cudaGetSymbolAddress, done once per device with it current); make that
- *   first call before any stream capture.
+ *   cudaGetSymbolAddress with the device current), and so does the first
+ *   call after the device's context was replaced (e.g. by cudaDeviceReset):
+ *   the address is cached per context.  Make that first call before any
+ *   stream capture.
  *   All calls share the one array: calls whose kernels overlap on the GPU
  *   (other streams, other threads, other plans) race and corrupt each
  *   other's images.  Calls ordered on one stream are safe; leftover contents
@@ -217,6 +223,11 @@ int psfsim_adjoint(psfsim_t h, const float *d_g, int B, float *d_gx, void *d_scr
 /* Block until `stream` drains, then report a device-side status recorded by
  * this plan's kernels (PSFSIM_ERR_TIMEOUT if a bounded wait gave up). */
 int psfsim_sync_status(psfsim_t h, void *stream);
+
+/* Clear the plan's device status word (enqueued on `stream`), so that a
+ * later psfsim_sync_status reports only what happens after this call.  The
+ * word is sticky otherwise: a timeout stays recorded until it is cleared. */
+int psfsim_reset_status(psfsim_t h, void *stream);
 
 /* Release the host handle.  Device buffers stay the caller's. */
 void psfsim_free(psfsim_t h);

@@ -10,6 +10,7 @@ Modules:
   psfsim_oracle  geometry (Eq. 2-3), radial lerp, bilinear rotation, A, A x, A^T g
   ring_oracle    exozodi ring model, its analytic parameter gradient, the fit loss
   split_oracle   split-BF16 (hi + lo with per-column power-of-two scale) encoding
+  convolution_oracle  direct FP64 convolution (the Sec. 3 comparison system)
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py`` against
 closed forms, invariants, brute force or library routines (see each docstring).

@@ -1,4 +1,5 @@
-"""ctypes declarations of libpsfsim's C ABI (include/psfsim.h, include/psfsim_fit.h).
+"""ctypes declarations of libpsfsim's C ABI (include/psfsim.h, include/psfsim_fit.h,
+include/psfsim_testing.h).
 
 Argument marshalling only: every step of the method runs in the CUDA library.
 Loading fails loudly when the library is missing; there is no fallback.
@@ -54,6 +55,8 @@ SIGNATURES = {
     "psfsim_forward_multi_scratch_bytes": (i32, [ctypes.POINTER(Job), i32, ctypes.POINTER(Tuning), c_size_p]),
     "psfsim_forward_multi": (i32, [ctypes.POINTER(Job), i32, ctypes.POINTER(Tuning), vp, ctypes.c_size_t, vp]),
     "psfsim_sync_status": (i32, [vp, vp]),
+    "psfsim_reset_status": (i32, [vp, vp]),
+    "psfsim_debug_forward_stall": (i32, [vp, vp, i32, vp, vp, ctypes.c_size_t, ctypes.c_uint64, i64, vp]),
     "psfsim_ring_chain_scratch_bytes": (i32, [i32, c_size_p]),
     "psfsim_loss_scratch_bytes": (i32, [i64, c_size_p]),
     "psfsim_ring_scene": (i32, [i32, f64, f64, vp, vp, vp]),

@@ -5,6 +5,7 @@
 #include <new>
 
 #include "psfsim_internal.cuh"
+#include "../../include/psfsim_testing.h"
 
 namespace {
 
@@ -309,6 +310,26 @@ int psfsim_sync_status(psfsim_t h, void *stream) {
   if (cudaMemcpy(&status, h->ws + h->status_off, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return PSFSIM_ERR_CUDA;
   return status;
+}
+
+int psfsim_reset_status(psfsim_t h, void *stream) {
+  if (!h) return PSFSIM_ERR_ARG;
+  return cudaMemsetAsync(h->ws + h->status_off, 0, sizeof(int), static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? PSFSIM_OK
+             : PSFSIM_ERR_CUDA;
+}
+
+int psfsim_debug_forward_stall(psfsim_t h, const float *d_x, int B, float *d_y, void *d_scratch,
+                               size_t scratch_bytes, uint64_t wait_ns, int64_t stall_load, void *stream) {
+  if (!h || !d_x || !d_y || B < 1 || B > 80) return PSFSIM_ERR_ARG;
+  if (wait_ns < 1000 || wait_ns > 2000000000ull || stall_load < -1) return PSFSIM_ERR_ARG;
+  if (h->storage != PSFSIM_SPLIT_BF16 && h->storage != PSFSIM_BF16) return PSFSIM_ERR_UNSUPPORTED;
+  const size_t need = psfsim_forward_tc_scratch(h, B);
+  if (!d_scratch || !aligned(d_scratch, 256) || scratch_bytes < need) return PSFSIM_ERR_WORKSPACE;
+  return psfsim_launch_forward_tc_stall(h, d_x, B, d_y, d_scratch, wait_ns, stall_load,
+                                        static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? PSFSIM_OK
+             : PSFSIM_ERR_CUDA;
 }
 
 void psfsim_free(psfsim_t h) { delete h; }

@@ -250,12 +250,17 @@ __global__ void __launch_bounds__(512) build_fp32_kernel(const __grid_constant__
         ptx::tma_load_3d(s0, &map, -4, -1, k, &mbar);
       }
       if (!ptx::mbar_wait_bounded(&mbar, phase)) failed = true;
-      phase ^= 1u;
       cur_k = k;
       if (__syncthreads_or(failed)) {
-        if (threadIdx.x == 0) atomicExch(P.status, PSFSIM_ERR_TIMEOUT);
+        // The copy may still be landing in shared memory: give it one more
+        // bounded wait before the CTA exits.
+        if (threadIdx.x == 0) {
+          ptx::mbar_wait_bounded(&mbar, phase);
+          atomicExch(P.status, PSFSIM_ERR_TIMEOUT);
+        }
         return;
       }
+      phase ^= 1u;
     }
     for (int64_t c = pos + warp; c < gend; c += nwarps) {
       const int j = P.order[c];

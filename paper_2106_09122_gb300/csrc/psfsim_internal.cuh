@@ -72,6 +72,10 @@ size_t psfsim_forward_tc_scratch(const psfsim_plan *h, int B);
 cudaError_t psfsim_launch_forward_tc(const psfsim_plan *h, const float *x, int B, float *y, void *scratch,
                                      cudaStream_t st);
 size_t psfsim_adjoint_split_scratch(const psfsim_plan *h, int B);
+// Test hook: the tensor-core forward of <= 80 scenes on one CTA with every
+// wait bounded by wait_ns and load number stall_it never issued.
+cudaError_t psfsim_launch_forward_tc_stall(const psfsim_plan *h, const float *x, int B, float *y, void *scratch,
+                                           uint64_t wait_ns, int64_t stall_it, cudaStream_t st);
 // Multi-job persistent tensor-core forward (several split-BF16 plans, one launch).
 int psfsim_multi_validate(const psfsim_job_t *jobs, int njobs);
 size_t psfsim_forward_multi_scratch(const psfsim_job_t *jobs, int njobs, const psfsim_tuning_t *tune);

@@ -66,6 +66,8 @@ struct TcMulti {
   int interleave;  // jobs share one A and one unit count: unit u is job u % njobs, unit u / njobs
   uint32_t tmem_cols, acc_stride;
   int *status;
+  uint64_t wait_ns;  // limit of every bounded wait
+  int64_t stall_it;  // test hook: the producer never issues this load (-1: none)
 };
 
 __global__ void xsplit_kernel(const float *__restrict__ x, int B, const int *__restrict__ count, int Bp, int64_t K,
@@ -117,15 +119,18 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], tfull_bar[2], tempty_bar[2];
+  __shared__ __align__(8) uint64_t drain_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint64_t lim = P.wait_ns;
   if (threadIdx.x == 0) {
     for (int s = 0; s < P.stages; ++s) {
       ptx::mbar_init(&full_bar[s], 1);
       ptx::mbar_init(&empty_bar[s], 1);
     }
+    ptx::mbar_init(&drain_bar, 1);
     for (int a = 0; a < 2; ++a) {
       ptx::mbar_init(&tfull_bar[a], 1);
       ptx::mbar_init(&tempty_bar[a], 4);
@@ -154,11 +159,12 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
       const uint32_t tx = (J.has_lo ? 2 : 1) * kTileBytes + (uint32_t)(J.xparts * J.Bp) * BK * 2;
       for (int kt = k_begin(J, ks); kt < k_begin(J, ks + 1); ++kt, ++it) {
         const int s = (int)(it % P.stages);
-        if (!ptx::mbar_wait_bounded(&empty_bar[s], ((it / P.stages) & 1) ^ 1)) {
+        if (!ptx::mbar_wait_bounded(&empty_bar[s], ((it / P.stages) & 1) ^ 1, lim)) {
           set_abort(&abort_flag, P.status);
           ok = false;
           break;
         }
+        if ((int64_t)it == P.stall_it) continue;  // test hook: this stage is never filled
         uint8_t *st = smem + (size_t)s * P.stage_bytes;
         ptx::mbar_arrive_expect_tx(&full_bar[s], tx);
         ptx::tma_load_2d(st, &P.map[jb][0], kt * BK, mt * BM, &full_bar[s]);
@@ -166,6 +172,13 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
         ptx::tma_load_2d(st + P.x_off, &P.map[jb][2], kt * BK, 0, &full_bar[s]);
       }
     }
+    // Drain: the last `stages` loads issued may not have been consumed (after
+    // a timeout the MMA issuer stops early); wait for each to land so that no
+    // copy into this CTA's shared memory is in flight when the CTA exits.
+    // Nothing re-armed these stages afterwards, so their phases are final.
+    for (uint32_t i = it > (uint32_t)P.stages ? it - (uint32_t)P.stages : 0u; i < it; ++i)
+      if ((int64_t)i != P.stall_it && !ptx::mbar_wait_bounded(&full_bar[i % P.stages], (i / P.stages) & 1, lim))
+        set_abort(&abort_flag, P.status);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
     uint32_t it = 0, c = 0;
@@ -182,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
       for (int kc = k0; kc < k1 && ok; kc += P.chunk, ++c) {
         const int kc1 = min(kc + P.chunk, k1);
         const uint32_t acc = c & 1;
-        if (!ptx::mbar_wait_bounded(&tempty_bar[acc], ((c >> 1) & 1) ^ 1)) {
+        if (!ptx::mbar_wait_bounded(&tempty_bar[acc], ((c >> 1) & 1) ^ 1, lim)) {
           set_abort(&abort_flag, P.status);
           ok = false;
           break;
@@ -191,7 +204,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
         const uint32_t d_tmem = tbase + acc * P.acc_stride;
         for (int kt = kc; kt < kc1; ++kt, ++it) {
           const int s = (int)(it % P.stages);
-          if (!ptx::mbar_wait_bounded(&full_bar[s], (it / P.stages) & 1)) {
+          if (!ptx::mbar_wait_bounded(&full_bar[s], (it / P.stages) & 1, lim)) {
             set_abort(&abort_flag, P.status);
             ok = false;
             break;
@@ -212,6 +225,10 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
         if (ok) ptx::mma_commit(&tfull_bar[acc]);
       }
     }
+    // Drain: wait until every MMA this thread issued has completed, so that
+    // none still reads shared memory or writes TMEM when the CTA releases them.
+    ptx::mma_commit(&drain_bar);
+    if (!ptx::mbar_wait_bounded(&drain_bar, 0, lim)) set_abort(&abort_flag, P.status);
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
     // The tensor core's FP32 accumulation is not rounded to nearest, so its
@@ -239,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
         const uint32_t acc = c & 1;
         int good = 0;
         if (lane == 0) {
-          good = !abort_flag && ptx::mbar_wait_bounded(&tfull_bar[acc], (c >> 1) & 1);
+          good = !abort_flag && ptx::mbar_wait_bounded(&tfull_bar[acc], (c >> 1) & 1, lim);
           if (!good) set_abort(&abort_flag, P.status);
         }
         good = __shfl_sync(0xffffffffu, good, 0);
@@ -248,7 +265,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_gemm_kernel(const __grid_const
           break;
         }
         // Already complete (lane 0 saw it): this gives every lane its acquire.
-        if (!ptx::mbar_wait_bounded(&tfull_bar[acc], (c >> 1) & 1)) set_abort(&abort_flag, P.status);
+        if (!ptx::mbar_wait_bounded(&tfull_bar[acc], (c >> 1) & 1, lim)) set_abort(&abort_flag, P.status);
         ptx::tc_fence_after();
         const uint32_t tacc = tbase + ((uint32_t)(quarter * 32) << 16) + acc * P.acc_stride;
 #pragma unroll
@@ -429,7 +446,17 @@ MultiPlan plan_multi(const JobSpec *jobs, int nj, const psfsim_tuning_t *tune) {
   return mp;
 }
 
-cudaError_t launch_multi(const JobSpec *jobs, int nj, const MultiPlan &mp, void *scratch, cudaStream_t st) {
+// Test hook of a launch: a short wait limit, one load the producer never
+// issues, and a single CTA (see psfsim_debug_forward_stall).
+struct StallHook {
+  uint64_t wait_ns;
+  int64_t stall_it;
+  bool one_cta;
+};
+constexpr StallHook kNoStall = {2000000000ull, -1, false};
+
+cudaError_t launch_multi(const JobSpec *jobs, int nj, const MultiPlan &mp, void *scratch, cudaStream_t st,
+                         const StallHook &hook = kNoStall) {
   char *base = static_cast<char *>(scratch);
   cudaError_t e;
   TcMulti P;  // kernel parameter block, copied at launch
@@ -477,11 +504,13 @@ cudaError_t launch_multi(const JobSpec *jobs, int nj, const MultiPlan &mp, void 
   P.stage_bytes = mp.stage_bytes;
   P.x_off = mp.x_off;
   P.status = reinterpret_cast<int *>(jobs[0].h->ws + jobs[0].h->status_off);
+  P.wait_ns = hook.wait_ns;
+  P.stall_it = hook.stall_it;
   if ((e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mp.smem)) !=
       cudaSuccess)
     return e;
   const int num_sms = jobs[0].h->num_sms;
-  const int slots = num_sms * mp.ctas_per_sm;
+  const int slots = hook.one_cta ? 1 : num_sms * mp.ctas_per_sm;
   tc_gemm_kernel<<<mp.units < slots ? mp.units : slots, kThreads, mp.smem, st>>>(P);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int j = 0; j < nj; ++j) {
@@ -555,4 +584,13 @@ cudaError_t psfsim_launch_forward_multi(const psfsim_job_t *jobs, int njobs, con
   JobSpec js[kMaxJobs];
   for (int j = 0; j < njobs; ++j) js[j] = JobSpec{jobs[j].plan, jobs[j].d_x, jobs[j].d_y, jobs[j].capacity, jobs[j].d_count};
   return launch_multi(js, njobs, plan_multi(js, njobs, tune), scratch, st);
+}
+
+cudaError_t psfsim_launch_forward_tc_stall(const psfsim_plan *h, const float *x, int B, float *y, void *scratch,
+                                           uint64_t wait_ns, int64_t stall_it, cudaStream_t st) {
+  JobSpec js[kMaxJobs];
+  const int nj = tc_jobs(h, x, B, y, js);
+  if (nj != 1) return cudaErrorInvalidValue;
+  const StallHook hook = {wait_ns, stall_it, true};
+  return launch_multi(js, nj, plan_multi(js, nj, nullptr), scratch, st, hook);
 }

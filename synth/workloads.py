@@ -94,6 +94,18 @@ def uneven_buckets() -> list[tuple[int, float]]:
     return [(N, S) for N in (64, 96, 128, 192, 256) for S in (0.3, 0.5)]
 
 
+def uneven_arrivals(count: int = 500, wave: int = 50, seed: int = BASE_SEED + 2 + 9):
+    """Seeded arrival order of the uneven workload's scenes (one (N, S) bucket each), its waves
+    of `wave` scenes, and the per-bucket capacity a wave needs (the most scenes any wave holds
+    of one bucket)."""
+    buckets = uneven_buckets()
+    rng = np.random.default_rng(seed)
+    order = [buckets[i] for i in rng.integers(0, len(buckets), count)]
+    waves = [order[i:i + wave] for i in range(0, len(order), wave)]
+    cap = max(max(wv.count(k) for k in buckets) for wv in waves)
+    return order, waves, cap
+
+
 def plain_small_scene(w: Workload) -> np.ndarray:
     img = scenes.ring_image(w.N, w.S, 5.0, 1.0, np.deg2rad(60.0), 0.3, 1e-9, w.r_max)
     rng = np.random.default_rng(w.seed)

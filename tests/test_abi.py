@@ -97,3 +97,9 @@ def test_products_reject_null_handles(lib):
     assert lib.psfsim_adjoint(None, None, 1, None, None, 0, None) == B.ERR_ARG
     assert lib.psfsim_info(None, None) == B.ERR_ARG
     lib.psfsim_free(None)
+
+
+def test_status_and_testing_hooks_reject_null_handles(lib):
+    assert lib.psfsim_reset_status(None, None) == B.ERR_ARG
+    assert lib.psfsim_sync_status(None, None) == B.ERR_ARG
+    assert lib.psfsim_debug_forward_stall(None, None, 1, None, None, 0, 1_000_000, 0, None) == B.ERR_ARG

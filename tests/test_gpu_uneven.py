@@ -78,3 +78,50 @@ def test_graph_replayed_waves_of_different_composition():
         out = server.run_wave(wave)
         for (k, x), y in zip(wave, out):
             _check(y.numpy(), As[k], x)
+
+
+@pytest.mark.parametrize("capacity", [None, 48])
+def test_full_size_uneven_launch_against_oracle_rows(capacity):
+    """The uneven workload's launch at full size: all 10 (N, S) buckets with their own
+    split-BF16 A (16384 x N^2) on the 128^2 library, one multi-job persistent launch, with
+    the capacity the bench's waves need (narrow accumulators, two CTAs per SM) and with 48
+    scenes per bucket (wide accumulators, one CTA per SM).  Uneven counts, one of them zero;
+    64 seeded rows per bucket against the oracle, every present scene."""
+    from paper_2106_09122_gb300 import Plan
+    from paper_2106_09122_gb300.serve import MultiForward
+    from synth import workloads
+    w = workloads.adjoint_128()
+    lib32 = w.library().astype(np.float32)
+    lib = torch.from_numpy(lib32).to(DEV)
+    buckets = workloads.uneven_buckets()
+    cap = capacity or workloads.uneven_arrivals(500, 50, w.seed + 9)[2]
+    plans = [Plan(lib, w.radii, w.s, N=k[0], S=k[1], storage="split_bf16") for k in buckets]
+    mf = MultiForward(plans, [cap] * len(buckets))
+    rng = np.random.default_rng(404 + cap)
+    counts = rng.integers(1, cap + 1, len(buckets))
+    counts[3] = 0
+    counts[7] = cap
+    X = []
+    for j, k in enumerate(buckets):
+        xs = np.stack([workloads.random_ring_scene(k[0], k[1], w.r_max, 50000 + 100 * j + b).ravel()
+                       for b in range(cap)]).astype(np.float32)
+        X.append(xs)
+        mf.x[j].copy_(torch.from_numpy(xs))
+        mf.y[j].fill_(float("nan"))
+    mf.count.copy_(torch.from_numpy(counts.astype(np.int32)))
+    mf.enqueue()
+    torch.cuda.synchronize()
+    assert plans[0].sync_status() == 0
+    for j, k in enumerate(buckets):
+        rows = np.sort(np.random.default_rng(j).choice(w.M, 64, replace=False))
+        xo, yo = O.scene_offsets(k[0], k[1])
+        A_r = O.A_rows(lib32.astype(np.float64), w.radii, xo, yo, rows)
+        y = mf.y[j].cpu().numpy()
+        nb = int(counts[j])
+        Xb = X[j][:nb].astype(np.float64)
+        if nb:
+            rel = O.bound_relative_error(y[:nb][:, rows], Xb @ A_r.T, np.abs(Xb) @ np.abs(A_r).T, floor=O.FLT_MIN)
+            assert rel.max() <= 1e-5, (k, rel.max())
+        assert np.all(np.isnan(y[nb:]))           # slots beyond the count are not written
+    for p in plans:
+        p.free()
