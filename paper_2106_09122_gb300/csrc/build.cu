@@ -303,8 +303,9 @@ WsLayout psfsim_layout(int n, int64_t K, int storage, int n_r) {
   L.pts_off = take(K * 16);
   L.status_off = take(16);
   L.libmax_off = take(PSFSIM_MAX_RADII * 4);
-  // FUSED keeps a copy of the library in quad layout (2 x 2 footprints as float4).
-  L.plib_off = storage == PSFSIM_FUSED ? take((int64_t)n_r * (n + 1) * (n + 1) * 16) : -1;
+  // FUSED keeps the library as pair entries (both PSFs of a radial bracket,
+  // each pixel's 2 x 2 bilinear footprint in difference form, 32 bytes).
+  L.plib_off = storage == PSFSIM_FUSED ? take(psfsim_pair_library_bytes(n, n_r)) : -1;
   L.total = off;
   (void)n_r;
   return L;
@@ -360,7 +361,7 @@ cudaError_t psfsim_launch_build(psfsim_plan *h, cudaStream_t st) {
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
       return e;
     h->K_valid = kv;
-    if (h->storage == PSFSIM_FUSED) return psfsim_launch_quad_library(h, st);
+    if (h->storage == PSFSIM_FUSED) return psfsim_launch_pair_library(h, st);
     // Compact split-BF16 rows hold just the valid columns (the layout reserved
     // the whole quadrant, an upper bound, before the count was known).
     if (h->storage == PSFSIM_SPLIT_BF16_SYM) h->ld = psfsim_round_up(kv > 0 ? kv : 1, 64);

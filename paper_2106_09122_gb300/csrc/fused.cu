@@ -1,27 +1,55 @@
 // Fused on-the-fly S = A Z: A is never stored.  Tiles of A are regenerated
 // from the radial library (lerp + bilinear rotation, Sec. 2) straight into
-// shared memory in the layout the tensor cores read, and multiplied there —
+// shared memory in the layout the tensor cores read, and multiplied there --
 // the paper's "standard interpolation method" (rebuild every time, Table 4)
 // done on chip, for scenes whose A does not fit in memory.
 //
 // Exact quadrant symmetry: with fixed-point rotation coordinates the column of
-// scene pixel R(j) = (-y, x) is bit-exactly the quarter-turned column of
-// pixel j = (x, y).  Only the x > 0, y > 0 quadrant Q0 is generated (columns
-// beyond the last radius are skipped), and
+// scene pixel R(j) = (-y, x) is exactly the quarter-turned column of pixel
+// j = (x, y).  Only the x > 0, y > 0 quadrant Q0 is generated (columns beyond
+// the last radius are skipped), and
 //     S = sum_{m=0..3} P^m (A_Q0 X^(m)),   X^(m)_j = x_{R^m(j)},
 // where P permutes image pixels by a quarter turn.  The four rotated copies of
 // each scene ride along the MMA's N dimension; x is split exactly into two
-// bf16 parts (x1 | x2) and A into hi + lo, so per k-step
-//     D[:, 0:8Bp] += hi [x1 x2]^T,  D[:, 0:4Bp] += lo [x1]^T.
-// The epilogue applies P^m as a scatter into per-rotation partial images that
-// are summed in a fixed order afterwards.
+// bf16 parts x1 + x2 and A into hi + lo, so per k-step three MMAs of N = 4Bp
+// accumulate into one TMEM accumulator D:
+//     D += hi x1^T,  D += hi x2^T,  D += lo x1^T
+// (only lo x2, < 2^-18 relative, is dropped).  The epilogue applies P^m as a
+// scatter into per-rotation partial images that are summed in a fixed order
+// afterwards.
 //
-// Warps: 0 TMA producer (x tiles), 1 tcgen05.mma issuer, 2..17 generators.
-// Generator g = w - 2 builds 8 columns of a 64-row half of every 128 x 64
-// tile, two rows per lane (a column's entry and coordinates serve both), and
-// also drains the TMEM accumulator of rotation g/4 for rows 32*(w%4)..+31
-// into FP32 registers every kChunk k-tiles (the tensor core's FP32
-// accumulation is not round-to-nearest, so long accumulations drift).
+// Generation.  The library is kept as "pair entries": for every bracket pair
+// (L[k], L[k+1]) and padded pixel (p, q) in [-1, n-1]^2, one 32-byte entry
+// holding the 2 x 2 bilinear footprint of both PSFs, tap by tap,
+//     (L00, L00'), (L01, L01'), (L10, L10'), (L11, L11')
+// (L01 = L[p][q+1], L10 = L[p+1][q], primes for L[k+1]), so one 256-bit load
+// fetches everything an element needs.  Source coordinates are 64-bit
+// fixed point in units of 2^-41 pixel (the geometry's cos and sin are exact
+// integers in those units, so moving by whole pixels is exact): a per-(tile,
+// column) origin plus multiples of cos and sin.  The bilinear weights of each
+// axis come from the coordinate's fraction rounded to 32 bits, f, as two
+// floats, f and 2^32 - f, each converted from the exact integer, so every
+// weight -- also a tiny one next to the edge of a footprint -- is accurate
+// relative to itself up to the 2^-32 rounding of the coordinate; with all
+// four taps and weights non-negative an element carries no cancellation,
+// which keeps the faint pixels at the image's corners, built only from such
+// edge samples, within their bound.  The two PSFs of the pair are
+// interpolated at once with paired FP32 operations.
+//
+// Warps: 16, all generators (four per scheduler partition, so each thread
+// may hold 128 registers).  Thread 0 also issues the x tiles' TMA loads, and
+// for each stage the warp that finishes its part last issues the stage's
+// tcgen05.mma (one lane).  An M-tile is an 8 x 16 block of image pixels.
+// Warp g builds columns 4g .. 4g+3 of every 128 x 64 tile for all 128 rows:
+// lane l handles the pixels (l % 8, l / 8 + 4t), t = 0..3, i.e. tile row
+// 32t + l, so a warp's 32 simultaneous loads come from one compact 8 x 4
+// pixel patch.  Warps also drain the TMEM accumulator of rotation g / 4 for
+// rows 32 (g % 4) .. +31 every kChunk k-tiles into a running FP32 sum kept in
+// a third TMEM region (the tensor core's FP32 accumulation is not
+// round-to-nearest, so long accumulations drift; the sums are added on the
+// CUDA cores, and keeping them in TMEM leaves the registers to generation).
+// Every wait is bounded; after a timeout each role waits (bounded) for the
+// asynchronous work it issued before the CTA releases its memory.
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
@@ -32,84 +60,113 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BK = 64;
-constexpr int kGenWarps = 16;
-constexpr int kThreads = (2 + kGenWarps) * 32;
-constexpr int kMaxStages = 6;
-constexpr int kChunk = 8;
+constexpr int kWarps = 16;                   // every warp generates; see the file comment for roles
+constexpr int kThreads = kWarps * 32;
+constexpr int kMaxStages = 4;
+constexpr int kChunk = 5;                    // k-tiles per accumulation: 5 x 4 x 3 = 60 MMAs
 constexpr int kMaxBp = 32;
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kAccStride = 256;
+constexpr uint32_t kAccStride = 128;         // two accumulators of 4Bp <= 128 columns
+constexpr uint32_t kSumCol = 256;            // running sums: columns 256 .. 256 + 4Bp
 constexpr uint32_t kTileBytes = BM * BK * 2;
-
-// An M-tile is a 16 x 8 block of image pixels (tile row r -> pixel
-// (p0 + r / 16, q0 + r % 16)), so a warp's 32 rows form a 16 x 2 patch and its
-// bilinear taps touch few cache lines.
-constexpr int kBlockQ = 16, kBlockP = 8;
-constexpr int kTabTiles = 4;  // k-tiles per column table (one generator barrier per table)
+constexpr int kTileW = 8, kTileH = 16;       // M-tile: 8 x 16 image pixels
+constexpr int kCols = BK / kWarps;           // columns per generator warp per k-tile
+constexpr int kSlots = BM / 32;              // tile rows per lane
+constexpr int kTabTiles = 4;                 // k-tiles per column table (one generator barrier each)
+static_assert(kTileW * kTileH == BM && kCols == 4 && kSlots == 4 && kWarps == 16, "tile shape");
+constexpr int kFixShift = PSFSIM_FRAC_BITS + 1;  // fraction bits of the source coordinates a and b
 
 struct FusedParams {
   int n, N, Bp, B, KS, m_tiles, k_tiles, stages, tiles_q;
-  int64_t M, rows, K0v, psz;  // psz: float4 entries per quad-layout PSF, (n + 1)^2
+  int64_t M, rows, K0v;
   uint32_t stage_bytes;
+  uint32_t pair_entries;  // entries per bracket pair, (n + 1)^2
+  uint32_t zero_entry;    // index of the all-zero entry after the last pair
   const ColGeom *geom;
   const int *order;
-  const float4 *qlib; // quad-layout library, [n_r][(n+1)^2]
-  float *part;        // [KS][4][B][M]
+  const float *plib;      // pair entries, 8 floats each
+  float *part;            // [KS][4][B][rows]
   int *status;
+  uint64_t wait_ns;
 };
 
-// Per-column constants of one k-tile, shared by the generator warps: the
-// fixed-point source coordinates of the tile's origin pixel and the steps.
-// The steps C = cos and S = sin (fixed point) are kept as (lo, hi) 32-bit
-// pieces so that offsets u >= 0 inside a tile cost one wide and one narrow
-// integer multiply-add each (exact modulo 2^64).
-struct ColEntry {
+// Per-column constants of one k-tile for the CTA's current M-tile, shared by
+// the generator warps.  Source column (+1) and row (+1) of tile pixel
+// (du, dv), du in [0, 8), dv in [0, 16), in units of 2^-41:
+//     a = A0 + C2 du + S2 dv,   b = B0 + S2 (7 - du) + C2 dv.
+struct __align__(16) ColEntry {
   long long A0, B0;
-  uint32_t Clo, Slo, NSlo;
-  int32_t Chi, Shi, NShi;
-  int64_t off;  // offset of L[k] in the quad-layout library (0 for padding columns)
-  float w0, w1;
+  unsigned long long C2, S2;  // cos, sin (both in [0, 1) for the quadrant) in units of 2^-41
+  uint32_t off;               // first pair entry of the column's bracket
+  float w0, w1;               // lerp weights of L[k] and L[k+1], times 2^-64
+  uint32_t pad;
+};
+static_assert(sizeof(ColEntry) == 48, "ColEntry layout");
+
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+
+__device__ __forceinline__ void f2_unpack(uint64_t v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+// Two FP32 multiplies (round to nearest) on register pairs.
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// Two FP32 fused multiply-adds (round to nearest) on register pairs.
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// One 32-byte pair entry (read-only path): the four taps, each as the pair
+// (L[k], L[k+1]).
+struct Entry {
+  uint64_t t00, t01, t10, t11;
 };
 
-__device__ __forceinline__ long long fx_mad(long long base, uint32_t lo, int32_t hi, uint32_t u) {
-  uint64_t r = (uint64_t)base + (uint64_t)lo * u;
-  r += (uint64_t)(uint32_t)(hi * (int32_t)u) << 32;
-  return (long long)r;
+__device__ __forceinline__ Entry load_entry(const float *p) {
+  Entry e;
+  asm volatile("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
+               : "=l"(e.t00), "=l"(e.t01), "=l"(e.t10), "=l"(e.t11)
+               : "l"(p));
+  return e;
 }
 
-__device__ __forceinline__ void split64(long long v, uint32_t &lo, int32_t &hi) {
-  lo = (uint32_t)(unsigned long long)v;
-  hi = (int32_t)(v >> 32);
-}
-
-// The two bilinear weights of one axis from the 32-bit fixed-point fraction,
-// in units of 2^-32: the smaller one is converted (relative accuracy 2^-24),
-// the larger one is 2^32 - smaller, exact because the smaller is at most 2^31.
-// The two factors 2^-32 are applied as exact power-of-two scalings elsewhere:
-// one in the column weights w0, w1 of the table, one in the epilogue.
-__device__ __forceinline__ void axis_weights(unsigned f, float &w_lo_tap, float &w_hi_tap) {
-  const bool low = f <= 0x80000000u;
-  const float small = __uint2float_rn(low ? f : 0u - f);
-  const float large = 4294967296.f - small;
-  w_hi_tap = low ? small : large;
-  w_lo_tap = low ? large : small;
-}
-
-// Library in "quad" layout: for every padded pixel (p, q), p, q in [-1, n-1],
-// the float4 (L[p][q], L[p][q+1], L[p+1][q], L[p+1][q+1]) with zeros outside
-// the PSF, so the whole bilinear footprint of a sample is one aligned 16-byte
-// load.  Indexed [k][(p+1)(n+1) + (q+1)].
-__global__ void quad_library_kernel(const float *__restrict__ lib, int n, int n_r, float4 *__restrict__ qlib) {
+// Pair entries of the library (see the file comment); entry (k, p, q) at
+// k (n+1)^2 + (p+1)(n+1) + (q+1), plus one all-zero entry at the end.
+__global__ void pair_library_kernel(const float *__restrict__ lib, int n, int n_r, float *__restrict__ plib) {
   const int nq = n + 1;
-  const int64_t total = (int64_t)n_r * nq * nq;
+  const int64_t per = (int64_t)nq * nq;
+  const int64_t total = (int64_t)(n_r - 1) * per + 1;
   auto at = [&](int64_t k, int p, int q) -> float {
     return (p >= 0 && p < n && q >= 0 && q < n) ? lib[(k * n + p) * n + q] : 0.f;
   };
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k = t / ((int64_t)nq * nq);
-    const int rem = (int)(t % ((int64_t)nq * nq));
-    const int p = rem / nq - 1, q = rem % nq - 1;
-    qlib[t] = make_float4(at(k, p, q), at(k, p, q + 1), at(k, p + 1, q), at(k, p + 1, q + 1));
+    float e[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (t < total - 1) {
+      const int64_t k = t / per;
+      const int rem = (int)(t % per);
+      const int p = rem / nq - 1, q = rem % nq - 1;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        e[h] = at(k + h, p, q);
+        e[2 + h] = at(k + h, p, q + 1);
+        e[4 + h] = at(k + h, p + 1, q);
+        e[6 + h] = at(k + h, p + 1, q + 1);
+      }
+    }
+    float4 *dst = reinterpret_cast<float4 *>(plib + 8 * t);
+    dst[0] = make_float4(e[0], e[1], e[2], e[3]);
+    dst[1] = make_float4(e[4], e[5], e[6], e[7]);
   }
 }
 
@@ -140,56 +197,27 @@ __global__ void fused_xgather(const float *__restrict__ x, int B, int Bp, int N,
   }
 }
 
-// One A element, times 2^32, from a column-table entry and the pixel's
-// fixed-point source coordinates (a2, b2).  The 2 x 2 footprint of each PSF
-// is one float4 of the quad-layout library, so only the footprint position
-// (q0, p0 in [-1, n-1]) needs a check.  Padding columns have weights 0 and an
-// in-range footprint, so they give 0 without a test of their own.
-__device__ __forceinline__ float gen_element(const ColEntry &e, const float4 *__restrict__ qlib, int n,
-                                             int64_t qsz, long long a2, long long b2) {
-  constexpr int kShift = PSFSIM_FRAC_BITS + 1;
-  const int q0 = (int)(a2 >> kShift);
-  const int p0 = (int)(b2 >> kShift);
-  if ((unsigned)(q0 + 1) > (unsigned)n || (unsigned)(p0 + 1) > (unsigned)n) return 0.f;
-  float wa0, wa1, wb0, wb1;
-  axis_weights((unsigned)((unsigned long long)a2 >> (kShift - 32)), wa0, wa1);
-  axis_weights((unsigned)((unsigned long long)b2 >> (kShift - 32)), wb0, wb1);
-  const float4 *Q0 = qlib + e.off + (int64_t)(p0 + 1) * (n + 1) + (q0 + 1);
-  const float4 t0 = __ldg(Q0);
-  const float v0 = wb0 * (wa0 * t0.x + wa1 * t0.y) + wb1 * (wa0 * t0.z + wa1 * t0.w);
-  float v1 = 0.f;
-  if (e.w1 != 0.f) {
-    const float4 t1 = __ldg(Q0 + qsz);
-    v1 = wb0 * (wa0 * t1.x + wa1 * t1.y) + wb1 * (wa0 * t1.z + wa1 * t1.w);
-  }
-  return e.w0 * v0 + e.w1 * v1;
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-  const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
-  return (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
-}
-
 __device__ __forceinline__ void set_abort(volatile int *flag, int *status) {
   *flag = 1;
   atomicExch(status, PSFSIM_ERR_TIMEOUT);
 }
 
 // Warp-uniform bounded wait: lane 0 decides, every lane then takes the acquire.
-__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *status) {
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *status,
+                                          uint64_t lim) {
   const int lane = threadIdx.x & 31;
   int ok = 0;
   if (lane == 0) {
-    ok = !*abort_flag && ptx::mbar_wait_bounded(bar, parity);
+    ok = !*abort_flag && ptx::mbar_wait_bounded(bar, parity, lim);
     if (!ok) set_abort(abort_flag, status);
   }
   ok = __shfl_sync(0xffffffffu, ok, 0);
-  if (ok && !ptx::mbar_wait_bounded(bar, parity)) set_abort(abort_flag, status);
+  if (ok && !ptx::mbar_wait_bounded(bar, parity, lim)) set_abort(abort_flag, status);
   return ok != 0;
 }
 
-// Named barrier over the generator warps that also ANDs a flag across them,
-// so every generator leaves the pipeline at the same point after a timeout.
+// Block-wide barrier that also ANDs a flag across the threads, so every warp
+// leaves the pipeline at the same point after a timeout.
 __device__ __forceinline__ bool gen_barrier_and(bool v) {
   uint32_t r;
   asm volatile(
@@ -198,32 +226,110 @@ __device__ __forceinline__ bool gen_barrier_and(bool v) {
       "bar.red.and.pred q, 1, %2, p;\n\t"
       "selp.u32 %0, 1, 0, q;\n\t}"
       : "=r"(r)
-      : "r"((uint32_t)v), "r"(kGenWarps * 32)
+      : "r"((uint32_t)v), "r"(kThreads)
       : "memory");
   return r != 0;
 }
 
 __device__ __forceinline__ int unit_k0(const FusedParams &P, int ks) { return (int)((int64_t)P.k_tiles * ks / P.KS); }
 
+// Column-table entry of sorted column t for the M-tile whose origin pixel is
+// (p0, q0); padding columns get an origin far outside the library (their
+// footprints are all the zero entry) and zero steps.
+__device__ __forceinline__ ColEntry column_entry(const FusedParams &P, int64_t t, int p0, int q0) {
+  ColEntry e;
+  // Padding: an origin far outside the library (every footprint is the zero
+  // entry) and zero steps.
+  e.A0 = e.B0 = -(1ll << 62);
+  e.C2 = e.S2 = 0ull;
+  e.off = 0u;
+  e.w0 = e.w1 = 0.f;
+  e.pad = 0u;
+  if (t < P.K0v) {
+    const ColGeom gm = P.geom[P.order[t]];
+    const long long h = P.n - 1;
+    // 2a and 2b in units of 2^-PSFSIM_FRAC_BITS, i.e. a and b in units of
+    // 2^-41; +1 pixel (2^42) for the padded index.
+    // Half a unit of 2^-32 (2^8) rounds the fraction the weights use.
+    const long long base = ((h + 2) << PSFSIM_FRAC_BITS) + (1ll << (kFixShift - 33));
+    e.A0 = base + gm.C * (2ll * q0 - h) + gm.Sn * (2ll * p0 - h);
+    e.B0 = base - gm.Sn * (2ll * (q0 + kTileW - 1) - h) + gm.C * (2ll * p0 - h);
+    e.C2 = (unsigned long long)(2 * gm.C);
+    e.S2 = (unsigned long long)(2 * gm.Sn);
+    e.off = (uint32_t)gm.k * P.pair_entries;
+    e.w0 = gm.w0 * 0x1p-64f;
+    e.w1 = gm.w1 * 0x1p-64f;
+  }
+  return e;
+}
+
+// The two bilinear weights of one axis, in units of 2^-32, from the 32-bit
+// fraction f of a source coordinate: (2^32 - f, f), each converted from the
+// exact integer (relative error 2^-24 however small).
+__device__ __forceinline__ void axis_weights(uint32_t f, float &w_near, float &w_far) {
+  w_far = __uint2float_rn(f);
+  w_near = f ? __uint2float_rn(0u - f) : 4294967296.f;
+}
+
+// MMAs of one stage (k-tile kt of chunk [kc, kc1)), issued by the generator
+// lane whose warp finished the stage last: wait for all generators and for the
+// x tile, and (first k-tile of a chunk) for the accumulator to be drained;
+// then 4 k-steps of three N = 4Bp MMAs, a commit that frees the stage, and
+// (last k-tile of the chunk) one that hands the accumulator to the drain.
+__device__ __forceinline__ void issue_stage_mmas(const FusedParams &P, uint8_t *stage, uint64_t *xfull,
+                                                 uint64_t *gfull, uint64_t *empty, uint64_t *tfull, uint64_t *tempty,
+                                                 uint32_t par, uint32_t c, bool first_kt, bool last_kt, uint32_t tbase,
+                                                 volatile int *abort_flag) {
+  const uint64_t lim = P.wait_ns;
+  const uint32_t acc = c & 1;
+  if (!ptx::mbar_wait_bounded(gfull, par, lim) || !ptx::mbar_wait_bounded(xfull, par, lim) ||
+      (first_kt && !ptx::mbar_wait_bounded(&tempty[acc], ((c >> 1) & 1) ^ 1, lim))) {
+    set_abort(abort_flag, P.status);
+    return;
+  }
+  ptx::tc_fence_after();
+  const uint32_t idesc = ptx::idesc_bf16_f32(BM, 4 * P.Bp);
+  const uint32_t x2_off = (uint32_t)(4 * P.Bp) * 128;  // x2 rows follow the 4Bp rows of x1
+  const uint64_t dh = ptx::smem_desc_sw128(stage);
+  const uint64_t dl = ptx::smem_desc_sw128(stage + kTileBytes);
+  const uint64_t dx1 = ptx::smem_desc_sw128(stage + 2 * kTileBytes);
+  const uint64_t dx2 = ptx::smem_desc_sw128(stage + 2 * kTileBytes + x2_off);
+  const uint32_t d_tmem = tbase + acc * kAccStride;
+#pragma unroll
+  for (int kk = 0; kk < BK / 16; ++kk) {
+    const uint64_t adv = (uint64_t)(kk * 32) >> 4;
+    ptx::mma_bf16(d_tmem, dh + adv, dx1 + adv, idesc, (!first_kt || kk > 0) ? 1u : 0u);
+    ptx::mma_bf16(d_tmem, dh + adv, dx2 + adv, idesc, 1u);
+    ptx::mma_bf16(d_tmem, dl + adv, dx1 + adv, idesc, 1u);
+  }
+  ptx::mma_commit(empty);
+  if (last_kt) ptx::mma_commit(&tfull[acc]);
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     fused_kernel(const __grid_constant__ CUtensorMap map_x, const FusedParams P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t xfull[kMaxStages], gfull[kMaxStages], empty[kMaxStages], tfull[2], tempty[2];
+  __shared__ __align__(8) uint64_t drain_bar;
+  __shared__ int arrivals[kMaxStages];
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
   __shared__ ColEntry ctab[2][kTabTiles * BK];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint64_t lim = P.wait_ns;
   if (threadIdx.x == 0) {
     for (int s = 0; s < P.stages; ++s) {
       ptx::mbar_init(&xfull[s], 1);
-      ptx::mbar_init(&gfull[s], kGenWarps);
+      ptx::mbar_init(&gfull[s], kWarps);
       ptx::mbar_init(&empty[s], 1);
+      arrivals[s] = 0;
     }
     for (int a = 0; a < 2; ++a) {
       ptx::mbar_init(&tfull[a], 1);
-      ptx::mbar_init(&tempty[a], kGenWarps);
+      ptx::mbar_init(&tempty[a], kWarps);
     }
+    ptx::mbar_init(&drain_bar, kWarps);
     abort_flag = 0;
     ptx::fence_mbar_init();
     ptx::prefetch_tensormap(&map_x);
@@ -238,224 +344,196 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tbase = tmem_base_sh;
   const int units = P.m_tiles * P.KS;
   const int Bp = P.Bp;
+  const bool producer = threadIdx.x == 0;  // also issues the x tiles' TMA loads
+  const uint32_t x_tx = (uint32_t)(8 * Bp) * BK * 2;
+  uint32_t x_issued = 0;                   // x loads issued (producer only)
 
-  if (warp == 0) {
-    if (lane == 0) {  // ---- TMA producer: x tiles ----
-      uint32_t it = 0;
-      const uint32_t tx = (uint32_t)(8 * Bp) * BK * 2;
-      for (int u = blockIdx.x; u < units && !abort_flag; u += gridDim.x) {
-        const int ks = u / P.m_tiles;
-        const int k0 = unit_k0(P, ks), k1 = unit_k0(P, ks + 1);
-        for (int kt = k0; kt < k1; ++kt, ++it) {
-          const int s = (int)(it % P.stages);
-          if (!ptx::mbar_wait_bounded(&empty[s], ((it / P.stages) & 1) ^ 1)) {
-            set_abort(&abort_flag, P.status);
-            break;
+  const int g = warp;                  // 0..15
+  const int quarter = warp & 3;        // TMEM lane quarter this warp may access
+  const int rot = g >> 2;              // rotation whose accumulator columns this warp drains
+  const int n = P.n;
+  const uint32_t un = (uint32_t)n;
+  const uint32_t nq = (uint32_t)(n + 1);
+  const uint32_t du = (uint32_t)(lane & 7);
+  const uint32_t ndu = (uint32_t)(kTileW - 1) - du;
+  const uint32_t dv0 = (uint32_t)(lane >> 3);
+  // Swizzled shared-memory address of this lane's 8 bytes (4 bf16 columns
+  // 4g..4g+3) in tile row 32t + lane: 16-byte chunk index XOR (row % 8)
+  // inside each 1024-byte group of 8 rows (128-byte swizzle).
+  const uint32_t row_off = (uint32_t)(lane >> 3) * 1024 + (uint32_t)(lane & 7) * 128 +
+                           (((uint32_t)(g >> 1) ^ (uint32_t)(lane & 7)) << 4) + (uint32_t)(g & 1) * 8;
+  uint32_t it = 0, c = 0, tg = 0;
+  const ColEntry *cur = ctab[0];
+  bool ok = true;
+  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+    const int ks = u / P.m_tiles, mt = u % P.m_tiles;
+    const int k0 = unit_k0(P, ks), k1 = unit_k0(P, ks + 1);
+    const int p0 = (mt / P.tiles_q) * kTileH, q0 = (mt % P.tiles_q) * kTileW;
+    // Running sums of this warp's rotation and lane quarter in TMEM.
+    const uint32_t tsum = tbase + ((uint32_t)(quarter * 32) << 16) + kSumCol + rot * Bp;
+    bool first = true;  // the unit's first drain writes the sums instead of adding
+    auto drain = [&](uint32_t cc) -> bool {
+      const uint32_t acc = cc & 1;
+      if (!warp_wait(&tfull[acc], (cc >> 1) & 1, &abort_flag, P.status, lim)) return false;
+      ptx::tc_fence_after();
+      const uint32_t tacc = tbase + ((uint32_t)(quarter * 32) << 16) + acc * kAccStride + rot * Bp;
+#pragma unroll
+      for (int qq = 0; qq < kMaxBp / 16; ++qq) {
+        if (qq * 16 < Bp) {
+          float v[16], sm[16];
+          ptx::tmem_ld16(tacc + qq * 16, v);
+          if (!first) ptx::tmem_ld16(tsum + qq * 16, sm);
+          ptx::tmem_ld_wait();
+          if (!first) {
+#pragma unroll
+            for (int t = 0; t < 16; ++t) v[t] += sm[t];
           }
-          ptx::mbar_arrive_expect_tx(&xfull[s], tx);
-          ptx::tma_load_2d(smem + (size_t)s * P.stage_bytes + 2 * kTileBytes, &map_x, kt * BK, 0, &xfull[s]);
+          ptx::tmem_st16(tsum + qq * 16, v);
         }
       }
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {  // ---- MMA issuer ----
-      const uint32_t idesc_hi = ptx::idesc_bf16_f32(BM, 8 * Bp);
-      const uint32_t idesc_lo = ptx::idesc_bf16_f32(BM, 4 * Bp);
-      uint32_t it = 0, c = 0;
-      bool ok = true;
-      for (int u = blockIdx.x; u < units && ok && !abort_flag; u += gridDim.x) {
-        const int ks = u / P.m_tiles;
-        const int k0 = unit_k0(P, ks), k1 = unit_k0(P, ks + 1);
-        for (int kc = k0; kc < k1 && ok; kc += kChunk, ++c) {
-          const int kc1 = min(kc + kChunk, k1);
-          const uint32_t acc = c & 1;
-          if (!ptx::mbar_wait_bounded(&tempty[acc], ((c >> 1) & 1) ^ 1)) {
-            set_abort(&abort_flag, P.status);
-            ok = false;
+      ptx::tmem_st_wait();
+      first = false;
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
+      return true;
+    };
+    // Every exit from this loop happens right after gen_barrier_and, which
+    // all warps reach the same number of times.
+    bool stop = false;
+    for (int kc = k0; kc < k1 && !stop; kc += kChunk, ++c) {
+      const int kc1 = min(kc + kChunk, k1);
+      for (int kt = kc; kt < kc1; ++kt, ++it) {
+        // Column table for the next kTabTiles k-tiles (double-buffered; one
+        // block-wide barrier per table, which also carries the abort decision).
+        if (((kt - k0) % kTabTiles) == 0) {
+          ColEntry *tab = ctab[tg & 1];
+          for (int e = threadIdx.x; e < kTabTiles * BK; e += kThreads) {
+            const int64_t t = (int64_t)kt * BK + e;
+            tab[e] = (kt + e / BK < k1) ? column_entry(P, t, p0, q0) : column_entry(P, P.K0v, p0, q0);
+          }
+          if (!gen_barrier_and(ok)) {
+            stop = true;
             break;
           }
-          ptx::tc_fence_after();
-          const uint32_t d_tmem = tbase + acc * kAccStride;
-          for (int kt = kc; kt < kc1; ++kt, ++it) {
-            const int s = (int)(it % P.stages);
-            const uint32_t par = (it / P.stages) & 1;
-            if (!ptx::mbar_wait_bounded(&xfull[s], par) || !ptx::mbar_wait_bounded(&gfull[s], par)) {
-              set_abort(&abort_flag, P.status);
-              ok = false;
-              break;
-            }
-            ptx::tc_fence_after();
-            const uint8_t *st = smem + (size_t)s * P.stage_bytes;
-            const uint64_t dh = ptx::smem_desc_sw128(st);
-            const uint64_t dl = ptx::smem_desc_sw128(st + kTileBytes);
-            const uint64_t dx = ptx::smem_desc_sw128(st + 2 * kTileBytes);
-#pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-              const uint64_t adv = (uint64_t)(kk * 32) >> 4;
-              ptx::mma_bf16(d_tmem, dh + adv, dx + adv, idesc_hi, (kt > kc || kk > 0) ? 1u : 0u);
-              ptx::mma_bf16(d_tmem, dl + adv, dx + adv, idesc_lo, 1u);
-            }
-            ptx::mma_commit(&empty[s]);
-          }
-          if (ok) ptx::mma_commit(&tfull[acc]);
+          cur = tab;
+          ++tg;
         }
-      }
-    }
-  } else {
-    // ---- generators (+ accumulator drain) ----
-    const int g = warp - 2;              // 0..15
-    const int gtid = g * 32 + lane;      // 0..511
-    const int quarter = warp & 3;        // TMEM lane quarter this warp may access
-    const int rot = g >> 2;              // rotation whose accumulator columns this warp drains
-    const int r = quarter * 32 + lane;   // tile row this lane drains
-    // Generation: this warp builds 8 columns (group g / 2) of the tile's 64-row
-    // half g % 2, two rows per lane: rA and rB = rA + 32, i.e. two image rows
-    // further down, whose source coordinates are rA's plus 2 (S, C) per column.
-    const int gc8 = g >> 1;
-    const int rA = 64 * (g & 1) + lane, rB = rA + 32;
-    const int n = P.n;
-    const long long h = n - 1;
-    const long long base = h << PSFSIM_FRAC_BITS;
-    const uint32_t du2 = 2 * (rA % kBlockQ), dv2 = 2 * (rA / kBlockQ);
-    uint32_t it = 0, c = 0, tg = 0;
-    const ColEntry *cur = ctab[0];
-    bool ok = true;
-    for (int u = blockIdx.x; u < units; u += gridDim.x) {
-      const int ks = u / P.m_tiles, mt = u % P.m_tiles;
-      const int k0 = unit_k0(P, ks), k1 = unit_k0(P, ks + 1);
-      const int po = (mt / P.tiles_q) * kBlockP, qo = (mt % P.tiles_q) * kBlockQ;
-      const int p = po + r / kBlockQ, q = qo + r % kBlockQ;
-      const bool row_ok = p < n && q < n;
-      const bool okA = po + rA / kBlockQ < n && qo + rA % kBlockQ < n;
-      const bool okB = po + rB / kBlockQ < n && qo + rB % kBlockQ < n;
-      const long long uo = 2 * qo - h, vo = 2 * po - h;
-      float sum[kMaxBp];
+        if (!ok) continue;  // after a timeout: no more work until the next barrier exits
+        const ColEntry *tab = cur + ((kt - k0) % kTabTiles) * BK + g * kCols;
+        const int s = (int)(it % P.stages);
+        const uint32_t par = (it / P.stages) & 1;
+        if (!warp_wait(&empty[s], par ^ 1, &abort_flag, P.status, lim)) {
+          ok = false;
+          continue;
+        }
+        uint8_t *stage = smem + (size_t)s * P.stage_bytes;
+        if (producer) {
+          ptx::mbar_arrive_expect_tx(&xfull[s], x_tx);
+          ptx::tma_load_2d(stage + 2 * kTileBytes, &map_x, kt * BK, 0, &xfull[s]);
+          ++x_issued;
+        }
+        float y[kSlots][kCols];
 #pragma unroll
-      for (int t = 0; t < kMaxBp; ++t) sum[t] = 0.f;
-      auto drain = [&](uint32_t cc) -> bool {
-        const uint32_t acc = cc & 1;
-        if (!warp_wait(&tfull[acc], (cc >> 1) & 1, &abort_flag, P.status)) return false;
-        ptx::tc_fence_after();
-        const uint32_t tacc = tbase + ((uint32_t)(quarter * 32) << 16) + acc * kAccStride + rot * Bp;
+        for (int cc = 0; cc < kCols; ++cc) {
+          const ColEntry ce = tab[cc];
+          const unsigned long long abase = ce.C2 * du + (unsigned long long)ce.A0;
+          const unsigned long long bbase = ce.S2 * ndu + (unsigned long long)ce.B0;
+          // All four rows' loads in flight before any is used.
+          Entry ent[kSlots];
+          uint32_t fa[kSlots], fb[kSlots];
 #pragma unroll
-        for (int qq = 0; qq < kMaxBp / 16; ++qq) {
-          if (qq * 16 < Bp) {
-            float v1[16], v2[16];
-            ptx::tmem_ld16(tacc + qq * 16, v1);
-            ptx::tmem_ld16(tacc + 4 * Bp + qq * 16, v2);
-            ptx::tmem_ld_wait();
+          for (int t = 0; t < kSlots; ++t) {
+            const uint32_t dv = dv0 + 4u * (uint32_t)t;
+            const unsigned long long a = ce.S2 * dv + abase;
+            const unsigned long long b = ce.C2 * dv + bbase;
+            const uint32_t qa = (uint32_t)(a >> kFixShift), pb = (uint32_t)(b >> kFixShift);
+            const bool inside = qa <= un && pb <= un;
+            const uint32_t idx = inside ? ce.off + pb * nq + qa : P.zero_entry;
+            ent[t] = load_entry(P.plib + 8 * (size_t)idx);
+            fa[t] = (uint32_t)(a >> (kFixShift - 32));
+            fb[t] = (uint32_t)(b >> (kFixShift - 32));
+          }
 #pragma unroll
-            for (int t = 0; t < 16; ++t) sum[qq * 16 + t] += v1[t] + v2[t];
+          for (int t = 0; t < kSlots; ++t) {
+            float an, af, bn, bf;
+            axis_weights(fa[t], an, af);
+            axis_weights(fb[t], bn, bf);
+            const uint64_t an2 = f2_pack(an, an), af2 = f2_pack(af, af);
+            const uint64_t r0 = fma2(af2, ent[t].t01, mul2(an2, ent[t].t00));  // row p, both PSFs
+            const uint64_t r1 = fma2(af2, ent[t].t11, mul2(an2, ent[t].t10));  // row p + 1
+            const uint64_t v = fma2(f2_pack(bf, bf), r1, mul2(f2_pack(bn, bn), r0));
+            float v0, v1;
+            f2_unpack(v, v0, v1);
+            y[t][cc] = fmaf(ce.w1, v1, ce.w0 * v0);
           }
         }
-        ptx::tc_fence_before();
+        uint8_t *st = stage + row_off;
+#pragma unroll
+        for (int t = 0; t < kSlots; ++t) {
+          const __nv_bfloat162 h01 = __floats2bfloat162_rn(y[t][0], y[t][1]);
+          const __nv_bfloat162 h23 = __floats2bfloat162_rn(y[t][2], y[t][3]);
+          const __nv_bfloat162 l01 = __floats2bfloat162_rn(y[t][0] - __low2float(h01), y[t][1] - __high2float(h01));
+          const __nv_bfloat162 l23 = __floats2bfloat162_rn(y[t][2] - __low2float(h23), y[t][3] - __high2float(h23));
+          *reinterpret_cast<uint2 *>(st + t * 4096) =
+              make_uint2(*reinterpret_cast<const uint32_t *>(&h01), *reinterpret_cast<const uint32_t *>(&h23));
+          *reinterpret_cast<uint2 *>(st + kTileBytes + t * 4096) =
+              make_uint2(*reinterpret_cast<const uint32_t *>(&l01), *reinterpret_cast<const uint32_t *>(&l23));
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
-        return true;
-      };
-      // Every exit from this loop happens right after gen_barrier_and, which
-      // all generator warps reach the same number of times.
-      bool stop = false;
-      for (int kc = k0; kc < k1 && !stop; kc += kChunk, ++c) {
-        const int kc1 = min(kc + kChunk, k1);
-        for (int kt = kc; kt < kc1; ++kt, ++it) {
-          // Column table for the next kTabTiles k-tiles (double-buffered; one
-          // named barrier per table, which also carries the abort decision).
-          if (((kt - k0) % kTabTiles) == 0) {
-            ColEntry *tab = ctab[tg & 1];
-            for (int c = gtid; c < kTabTiles * BK; c += kGenWarps * 32) {
-              const int64_t t = (int64_t)kt * BK + c;
-              ColEntry e;  // padding: zero steps from the centre pixel, zero weights
-              e.off = 0;
-              e.A0 = e.B0 = base;
-              e.Clo = e.Slo = e.NSlo = 0;
-              e.Chi = e.Shi = e.NShi = 0;
-              e.w0 = e.w1 = 0.f;
-              if (t < P.K0v && kt + c / BK < k1) {
-                const ColGeom gm = P.geom[P.order[t]];
-                e.A0 = base + gm.C * uo + gm.Sn * vo;
-                e.B0 = base - gm.Sn * uo + gm.C * vo;
-                split64(gm.C, e.Clo, e.Chi);
-                split64(gm.Sn, e.Slo, e.Shi);
-                split64(-gm.Sn, e.NSlo, e.NShi);
-                e.off = (int64_t)gm.k * P.psz;
-                e.w0 = gm.w0 * 0x1p-32f;
-                e.w1 = gm.w1 * 0x1p-32f;
-              }
-              tab[c] = e;
-            }
-            if (!gen_barrier_and(ok)) {
-              stop = true;
-              break;
-            }
-            cur = tab;
-            ++tg;
+        if (lane == 0) {
+          ptx::mbar_arrive(&gfull[s]);
+          // The warp that completes the stage issues its MMAs (the counter
+          // only grows: every use of a stage adds kWarps).
+          if ((atomicAdd(&arrivals[s], 1) & (kWarps - 1)) == kWarps - 1) {
+            issue_stage_mmas(P, stage, &xfull[s], &gfull[s], &empty[s], tfull, tempty, par, c, kt == kc,
+                             kt == kc1 - 1, tbase, &abort_flag);
           }
-          if (!ok) continue;  // after a timeout: no more work until the next barrier exits
-          const ColEntry *tab = cur + ((kt - k0) % kTabTiles) * BK;
-          const int s = (int)(it % P.stages);
-          if (!warp_wait(&empty[s], ((it / P.stages) & 1) ^ 1, &abort_flag, P.status)) {
-            ok = false;
-            continue;
-          }
-          uint8_t *st = smem + (size_t)s * P.stage_bytes;
-          uint32_t hw[2][4], lw[2][4];
-#pragma unroll
-          for (int cc = 0; cc < 8; cc += 2) {
-            float vA[2], vB[2];
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-              const ColEntry &ce = tab[gc8 * 8 + cc + e];
-              const long long a2 = fx_mad(fx_mad(ce.A0, ce.Clo, ce.Chi, du2), ce.Slo, ce.Shi, dv2);
-              const long long b2 = fx_mad(fx_mad(ce.B0, ce.NSlo, ce.NShi, du2), ce.Clo, ce.Chi, dv2);
-              vA[e] = okA ? gen_element(ce, P.qlib, n, P.psz, a2, b2) : 0.f;
-              vB[e] = okB ? gen_element(ce, P.qlib, n, P.psz, fx_mad(a2, ce.Slo, ce.Shi, 4u),
-                                        fx_mad(b2, ce.Clo, ce.Chi, 4u))
-                          : 0.f;
-            }
-            uint32_t hp = pack_bf16(vA[0], vA[1]);
-            hw[0][cc >> 1] = hp;
-            lw[0][cc >> 1] =
-                pack_bf16(vA[0] - __uint_as_float(hp << 16), vA[1] - __uint_as_float(hp & 0xFFFF0000u));
-            hp = pack_bf16(vB[0], vB[1]);
-            hw[1][cc >> 1] = hp;
-            lw[1][cc >> 1] =
-                pack_bf16(vB[0] - __uint_as_float(hp << 16), vB[1] - __uint_as_float(hp & 0xFFFF0000u));
-          }
-          // 128-byte swizzle: 16-byte chunk index XOR (row % 8) inside each 1024-byte row group.
-#pragma unroll
-          for (int hr = 0; hr < 2; ++hr) {
-            const int rr = hr ? rB : rA;
-            const uint32_t row_off = (uint32_t)(rr >> 3) * 1024 + (uint32_t)(rr & 7) * 128;
-            const uint32_t chunk = (uint32_t)gc8 ^ (uint32_t)(rr & 7);
-            *reinterpret_cast<uint4 *>(st + row_off + chunk * 16) =
-                make_uint4(hw[hr][0], hw[hr][1], hw[hr][2], hw[hr][3]);
-            *reinterpret_cast<uint4 *>(st + kTileBytes + row_off + chunk * 16) =
-                make_uint4(lw[hr][0], lw[hr][1], lw[hr][2], lw[hr][3]);
-          }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          __syncwarp();
-          if (lane == 0) ptx::mbar_arrive(&gfull[s]);
         }
-        if (!stop && ok && kc > k0 && !drain(c - 1)) ok = false;
+        __syncwarp();
       }
-      if (stop) break;
-      if (ok && !drain(c - 1)) ok = false;
-      if (!ok) continue;  // the next unit's first barrier takes every generator out
-      if (row_ok) {
-        int pp = p, qp = q;  // P^rot: (p, q) -> (q, n-1-p), applied rot times
-        for (int t = 0; t < rot; ++t) {
-          const int nxt = qp;
-          qp = n - 1 - pp;
-          pp = nxt;
-        }
-        float *out = P.part + ((int64_t)(ks * 4 + rot) * P.B) * P.rows + (int64_t)pp * n + qp;
+      if (!stop && ok && kc > k0 && !drain(c - 1)) ok = false;
+    }
+    if (stop) break;
+    if (ok && !drain(c - 1)) ok = false;
+    if (!ok) continue;  // the next unit's first barrier takes every warp out
+    // This lane drains tile row 32 quarter + lane: pixel (l % 8, l / 8 + 4 quarter).
+    // The TMEM loads are warp-collective, so every lane takes part; only
+    // lanes whose pixel lies inside the image store.
+    const int p = p0 + (lane >> 3) + 4 * quarter, q = q0 + (lane & 7);
+    const bool inside = p < n && q < n;
+    int pp = p, qp = q;  // P^rot: (p, q) -> (q, n-1-p), applied rot times
+    for (int t = 0; t < rot; ++t) {
+      const int nxt = qp;
+      qp = n - 1 - pp;
+      pp = nxt;
+    }
+    float *out = P.part + ((int64_t)(ks * 4 + rot) * P.B) * P.rows + (int64_t)pp * n + qp;
 #pragma unroll
-        for (int t = 0; t < kMaxBp; ++t)
-          if (t < P.B) out[(int64_t)t * P.rows] = sum[t] * 0x1p-32f;
+    for (int qq = 0; qq < kMaxBp / 16; ++qq) {
+      if (qq * 16 < Bp) {
+        float v[16];
+        ptx::tmem_ld16(tsum + qq * 16, v);
+        ptx::tmem_ld_wait();
+        if (inside) {
+#pragma unroll
+          for (int t = 0; t < 16; ++t)
+            if (qq * 16 + t < P.B) out[(int64_t)(qq * 16 + t) * P.rows] = v[t];
+        }
       }
     }
+    ptx::tc_fence_before();
   }
+  // Drain before the memory is released: every lane that issued MMAs commits
+  // them to drain_bar (a thread with none arrives at once), and the copies of
+  // x the producer issued land.
+  if (lane == 0) ptx::mma_commit(&drain_bar);
+  if (producer) {
+    for (uint32_t i = x_issued > (uint32_t)P.stages ? x_issued - (uint32_t)P.stages : 0u; i < x_issued; ++i)
+      if (!ptx::mbar_wait_bounded(&xfull[i % P.stages], (i / P.stages) & 1, lim)) set_abort(&abort_flag, P.status);
+  }
+  if (lane == 0 && !ptx::mbar_wait_bounded(&drain_bar, 0, lim)) set_abort(&abort_flag, P.status);
   __syncthreads();
   if (warp == 0) {
     __syncwarp();
@@ -495,15 +573,25 @@ FusedPlanInfo fused_info(const psfsim_plan *h, int Bc) {
   FusedPlanInfo f;
   f.Bp = Bc <= 16 ? 16 : 32;
   f.rows = psfsim_round_up(h->M, BM);
-  f.tiles_q = (h->n + kBlockQ - 1) / kBlockQ;
-  f.m_tiles = f.tiles_q * ((h->n + kBlockP - 1) / kBlockP);
+  f.tiles_q = (h->n + kTileW - 1) / kTileW;
+  f.m_tiles = f.tiles_q * ((h->n + kTileH - 1) / kTileH);
   f.k_tiles = (int)((h->K_valid + BK - 1) / BK);
   if (f.k_tiles < 1) f.k_tiles = 1;
   f.ldx = (int64_t)f.k_tiles * BK;
+  // Split over k: the fewest splits whose last wave of units is nearly full.
   f.KS = 1;
-  while ((int64_t)f.m_tiles * f.KS < 2 * h->num_sms && f.KS * 2 <= f.k_tiles) f.KS *= 2;
+  double best = 0.0;
+  for (int ks = 1; ks <= 8 && ks <= f.k_tiles; ++ks) {
+    const int64_t units = (int64_t)f.m_tiles * ks;
+    const int64_t waves = (units + h->num_sms - 1) / h->num_sms;
+    const double eff = (double)units / (double)(waves * h->num_sms);
+    if (eff > best + 0.02) {
+      best = eff;
+      f.KS = ks;
+    }
+  }
   f.stage_bytes = (uint32_t)psfsim_round_up(2 * kTileBytes + 8 * f.Bp * BK * 2, 1024);
-  f.stages = (int)((200 * 1024) / f.stage_bytes);
+  f.stages = (int)((196 * 1024) / f.stage_bytes);
   if (f.stages > kMaxStages) f.stages = kMaxStages;
   f.smem = (size_t)f.stages * f.stage_bytes + 1024;
   f.xs_bytes = (size_t)psfsim_round_up(8ll * f.Bp * f.ldx * 2, 256);
@@ -513,9 +601,11 @@ FusedPlanInfo fused_info(const psfsim_plan *h, int Bc) {
 
 }  // namespace
 
-cudaError_t psfsim_launch_quad_library(psfsim_plan *h, cudaStream_t st) {
-  quad_library_kernel<<<h->num_sms * 4, 256, 0, st>>>(h->d_lib, h->n, h->n_r,
-                                                      reinterpret_cast<float4 *>(h->ws + h->plib_off));
+int64_t psfsim_pair_library_bytes(int n, int n_r) { return ((int64_t)(n_r - 1) * (n + 1) * (n + 1) + 1) * 32; }
+
+cudaError_t psfsim_launch_pair_library(psfsim_plan *h, cudaStream_t st) {
+  pair_library_kernel<<<h->num_sms * 4, 256, 0, st>>>(h->d_lib, h->n, h->n_r,
+                                                      reinterpret_cast<float *>(h->ws + h->plib_off));
   return cudaGetLastError();
 }
 
@@ -549,18 +639,20 @@ cudaError_t psfsim_launch_forward_fused(const psfsim_plan *h, const float *x, in
     P.KS = f.KS;
     P.m_tiles = f.m_tiles;
     P.tiles_q = f.tiles_q;
-    P.psz = (int64_t)(h->n + 1) * (h->n + 1);
     P.k_tiles = f.k_tiles;
     P.stages = f.stages;
     P.M = h->M;
     P.rows = f.rows;
     P.K0v = h->K_valid;
     P.stage_bytes = f.stage_bytes;
+    P.pair_entries = (uint32_t)((h->n + 1) * (h->n + 1));
+    P.zero_entry = (uint32_t)(h->n_r - 1) * P.pair_entries;
     P.geom = reinterpret_cast<const ColGeom *>(h->ws + h->geom_off);
     P.order = order;
-    P.qlib = reinterpret_cast<const float4 *>(h->ws + h->plib_off);
+    P.plib = reinterpret_cast<const float *>(h->ws + h->plib_off);
     P.part = part;
     P.status = status;
+    P.wait_ns = 2000000000ull;
     if ((e = cudaFuncSetAttribute(fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem)) !=
         cudaSuccess)
       return e;

@@ -49,7 +49,10 @@ struct WsLayout {
   int64_t ld, a_off, lo_off, scale_off, geom_off, order_off, bstart_off, pts_off, status_off, libmax_off, plib_off, total;
 };
 WsLayout psfsim_layout(int n, int64_t K, int storage, int n_r);
-cudaError_t psfsim_launch_quad_library(psfsim_plan *h, cudaStream_t st);
+// FUSED storage's copy of the library: one 32-byte pair entry per bracket
+// pair and padded pixel, plus a zero entry (fused.cu).
+int64_t psfsim_pair_library_bytes(int n, int n_r);
+cudaError_t psfsim_launch_pair_library(psfsim_plan *h, cudaStream_t st);
 
 // Kernel launchers (return cudaError_t of the launch).
 cudaError_t psfsim_launch_build(psfsim_plan *h, cudaStream_t st);
