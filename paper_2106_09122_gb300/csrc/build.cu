@@ -2,6 +2,7 @@
 // that write every column of A = [I_1 ... I_K] (Eq. 4-5).
 #include <cudaTypedefs.h>
 
+#include <climits>
 #include <cstring>
 
 #include "psfsim_internal.cuh"
@@ -119,6 +120,59 @@ __global__ void __launch_bounds__(1024) bracket_sort_kernel(const ColGeom *geom,
       __syncwarp();
     }
   }
+}
+
+// Within each radial bracket, orders the columns by polar angle (the sine in
+// fixed point, increasing over the x > 0, y > 0 quadrant; ties by column
+// index, so the order is deterministic).  One CTA per bracket sorts its
+// segment of the bracket-sorted list in shared memory (bitonic); a segment
+// longer than kAngleSortMax keeps its (bracket, angle bin) order.  Any
+// column order gives the same product; this one puts columns of nearly the
+// same angle next to each other, so neighbouring columns read nearly the
+// same library pixels for a given image pixel.
+constexpr int kAngleSortMax = 4096;
+__global__ void __launch_bounds__(1024) angle_sort_kernel(const ColGeom *geom, int n_r, int *order,
+                                                          const int *bstart) {
+  __shared__ long long key[kAngleSortMax];
+  __shared__ int val[kAngleSortMax];
+  const int k = blockIdx.x;
+  const int begin = bstart[k * PSFSIM_THETA_BINS], end = bstart[(k + 1) * PSFSIM_THETA_BINS];
+  const int m = end - begin;
+  if (m < 2 || m > kAngleSortMax) return;
+  int pow2 = 1;
+  while (pow2 < m) pow2 <<= 1;
+  for (int i = threadIdx.x; i < pow2; i += blockDim.x) {
+    if (i < m) {
+      const int j = order[begin + i];
+      key[i] = geom[j].Sn;
+      val[i] = j;
+    } else {
+      key[i] = LLONG_MAX;
+      val[i] = INT_MAX;
+    }
+  }
+  __syncthreads();
+  for (int size = 2; size <= pow2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < pow2; i += blockDim.x) {
+        const int partner = i ^ stride;
+        if (partner > i) {
+          const bool up = (i & size) == 0;
+          const bool gt = key[i] > key[partner] || (key[i] == key[partner] && val[i] > val[partner]);
+          if (gt == up) {
+            const long long tk = key[i];
+            key[i] = key[partner];
+            key[partner] = tk;
+            const int tv = val[i];
+            val[i] = val[partner];
+            val[partner] = tv;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) order[begin + i] = val[i];
 }
 
 struct BuildParams {
@@ -361,7 +415,11 @@ cudaError_t psfsim_launch_build(psfsim_plan *h, cudaStream_t st) {
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
       return e;
     h->K_valid = kv;
-    if (h->storage == PSFSIM_FUSED) return psfsim_launch_pair_library(h, st);
+    if (h->storage == PSFSIM_FUSED) {
+      angle_sort_kernel<<<h->n_r - 1, 1024, 0, st>>>(geom, h->n_r, order, bstart);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      return psfsim_launch_pair_library(h, st);
+    }
     // Compact split-BF16 rows hold just the valid columns (the layout reserved
     // the whole quadrant, an upper bound, before the count was known).
     if (h->storage == PSFSIM_SPLIT_BF16_SYM) h->ld = psfsim_round_up(kv > 0 ? kv : 1, 64);

@@ -62,7 +62,7 @@ constexpr int BM = 128;
 constexpr int BK = 64;
 constexpr int kWarps = 16;                   // every warp generates; see the file comment for roles
 constexpr int kThreads = kWarps * 32;
-constexpr int kMaxStages = 4;
+constexpr int kMaxStages = 2;
 constexpr int kChunk = 5;                    // k-tiles per accumulation: 5 x 4 x 3 = 60 MMAs
 constexpr int kMaxBp = 32;
 constexpr uint32_t kTmemCols = 512;
@@ -434,38 +434,46 @@ __global__ void __launch_bounds__(kThreads, 1)
           ++x_issued;
         }
         float y[kSlots][kCols];
+        // Two columns at a time: all eight loads (two columns x four rows) are
+        // in flight before any is used.
 #pragma unroll
-        for (int cc = 0; cc < kCols; ++cc) {
-          const ColEntry ce = tab[cc];
-          const unsigned long long abase = ce.C2 * du + (unsigned long long)ce.A0;
-          const unsigned long long bbase = ce.S2 * ndu + (unsigned long long)ce.B0;
-          // All four rows' loads in flight before any is used.
-          Entry ent[kSlots];
-          uint32_t fa[kSlots], fb[kSlots];
+        for (int c2 = 0; c2 < kCols; c2 += 2) {
+          Entry ent[2][kSlots];
+          uint32_t fa[2][kSlots], fb[2][kSlots];
 #pragma unroll
-          for (int t = 0; t < kSlots; ++t) {
-            const uint32_t dv = dv0 + 4u * (uint32_t)t;
-            const unsigned long long a = ce.S2 * dv + abase;
-            const unsigned long long b = ce.C2 * dv + bbase;
-            const uint32_t qa = (uint32_t)(a >> kFixShift), pb = (uint32_t)(b >> kFixShift);
-            const bool inside = qa <= un && pb <= un;
-            const uint32_t idx = inside ? ce.off + pb * nq + qa : P.zero_entry;
-            ent[t] = load_entry(P.plib + 8 * (size_t)idx);
-            fa[t] = (uint32_t)(a >> (kFixShift - 32));
-            fb[t] = (uint32_t)(b >> (kFixShift - 32));
+          for (int h = 0; h < 2; ++h) {
+            const ColEntry ce = tab[c2 + h];
+            const unsigned long long abase = ce.C2 * du + (unsigned long long)ce.A0;
+            const unsigned long long bbase = ce.S2 * ndu + (unsigned long long)ce.B0;
+#pragma unroll
+            for (int t = 0; t < kSlots; ++t) {
+              const uint32_t dv = dv0 + 4u * (uint32_t)t;
+              const unsigned long long a = ce.S2 * dv + abase;
+              const unsigned long long b = ce.C2 * dv + bbase;
+              const uint32_t qa = (uint32_t)(a >> kFixShift), pb = (uint32_t)(b >> kFixShift);
+              const bool inside = qa <= un && pb <= un;
+              const uint32_t idx = inside ? ce.off + pb * nq + qa : P.zero_entry;
+              ent[h][t] = load_entry(P.plib + 8 * (size_t)idx);
+              fa[h][t] = (uint32_t)(a >> (kFixShift - 32));
+              fb[h][t] = (uint32_t)(b >> (kFixShift - 32));
+            }
           }
 #pragma unroll
-          for (int t = 0; t < kSlots; ++t) {
-            float an, af, bn, bf;
-            axis_weights(fa[t], an, af);
-            axis_weights(fb[t], bn, bf);
-            const uint64_t an2 = f2_pack(an, an), af2 = f2_pack(af, af);
-            const uint64_t r0 = fma2(af2, ent[t].t01, mul2(an2, ent[t].t00));  // row p, both PSFs
-            const uint64_t r1 = fma2(af2, ent[t].t11, mul2(an2, ent[t].t10));  // row p + 1
-            const uint64_t v = fma2(f2_pack(bf, bf), r1, mul2(f2_pack(bn, bn), r0));
-            float v0, v1;
-            f2_unpack(v, v0, v1);
-            y[t][cc] = fmaf(ce.w1, v1, ce.w0 * v0);
+          for (int h = 0; h < 2; ++h) {
+            const float w0 = tab[c2 + h].w0, w1 = tab[c2 + h].w1;
+#pragma unroll
+            for (int t = 0; t < kSlots; ++t) {
+              float an, af, bn, bf;
+              axis_weights(fa[h][t], an, af);
+              axis_weights(fb[h][t], bn, bf);
+              const uint64_t an2 = f2_pack(an, an), af2 = f2_pack(af, af);
+              const uint64_t r0 = fma2(af2, ent[h][t].t01, mul2(an2, ent[h][t].t00));  // row p, both PSFs
+              const uint64_t r1 = fma2(af2, ent[h][t].t11, mul2(an2, ent[h][t].t10));  // row p + 1
+              const uint64_t v = fma2(f2_pack(bf, bf), r1, mul2(f2_pack(bn, bn), r0));
+              float v0, v1;
+              f2_unpack(v, v0, v1);
+              y[t][c2 + h] = fmaf(w1, v1, w0 * v0);
+            }
           }
         }
         uint8_t *st = stage + row_off;
@@ -591,8 +599,10 @@ FusedPlanInfo fused_info(const psfsim_plan *h, int Bc) {
     }
   }
   f.stage_bytes = (uint32_t)psfsim_round_up(2 * kTileBytes + 8 * f.Bp * BK * 2, 1024);
-  f.stages = (int)((196 * 1024) / f.stage_bytes);
-  if (f.stages > kMaxStages) f.stages = kMaxStages;
+  // Two stages: a stage's MMAs take a fraction of the time its generation
+  // does, and the shared memory a third stage would take is worth more as
+  // L1 cache for the library footprints.
+  f.stages = 2;
   f.smem = (size_t)f.stages * f.stage_bytes + 1024;
   f.xs_bytes = (size_t)psfsim_round_up(8ll * f.Bp * f.ldx * 2, 256);
   f.part_bytes = (size_t)4 * f.KS * Bc * f.rows * 4;
