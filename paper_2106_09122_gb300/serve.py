@@ -4,10 +4,11 @@ Each (N, S) bucket has its own stored split-BF16 A (n^2 x N^2, Sec. 3 with
 n != N, s != S).  A wave of arriving scenes is simulated by ONE
 psfsim_forward_multi call: a persistent tensor-core launch whose work units
 interleave every bucket.  Scene counts per bucket live in device memory, so
-the whole wave (input gather, split, GEMM, reductions) is captured once in a
-CUDA graph and replayed for every wave whatever its composition.  The launch
-shape (drain chunk, units per SM, pipeline stages) is picked by `autotune`,
-which times candidate shapes on the actual job set.
+that launch (split, GEMM, reductions) is captured once in a CUDA graph and
+replayed for every wave whatever its composition; the copies around it move
+exactly the scenes present and the images written.  The launch shape (drain
+chunk, units per SM, pipeline stages) is picked by `autotune`, which times
+candidate shapes on the actual job set.
 """
 from __future__ import annotations
 
@@ -84,58 +85,104 @@ def autotune(mf: MultiForward, chunks=(2, 4, 8), units=(2, 4, 8), stages=(0,), r
 
 
 class UnevenServer:
-    """Serve waves of scenes of mixed (N, S) through one captured CUDA graph."""
+    """Serve waves of scenes of mixed (N, S) through one persistent multi-job launch.
+
+    A wave's scenes are grouped by bucket and stacked, one host copy per bucket,
+    into pinned staging (two sets, so the next wave is packed while the GPU works
+    on this one).  Only the bytes of the scenes present go to the device and only
+    the images written come back (one copy per non-empty bucket each way); the
+    multi-job forward itself, with its device-side counts, is one captured CUDA
+    graph replayed every wave.
+    """
 
     def __init__(self, plans: dict, capacity: int, tuning=None):
         self.keys = list(plans.keys())
+        self.index = {k: j for j, k in enumerate(self.keys)}
         self.mf = MultiForward([plans[k] for k in self.keys], [capacity] * len(self.keys), tuning)
         self.capacity = capacity
         self.graph = None
         dev = self.mf.plans[0].lib.device
-        self.h_count = torch.zeros(len(self.keys), dtype=torch.int32).pin_memory()
-        self.h_x = [torch.zeros((capacity, p.K), dtype=torch.float32).pin_memory() for p in self.mf.plans]
-        self.h_y = [torch.zeros((capacity, p.M), dtype=torch.float32).pin_memory() for p in self.mf.plans]
         self.stream = torch.cuda.Stream(device=dev)
-
-    def _wave_ops(self) -> None:
-        mf = self.mf
-        mf.count.copy_(self.h_count, non_blocking=True)
-        for j in range(len(self.keys)):
-            mf.x[j].copy_(self.h_x[j], non_blocking=True)
-        mf.enqueue(self.stream)
-        for j in range(len(self.keys)):
-            self.h_y[j].copy_(mf.y[j], non_blocking=True)
+        nb = len(self.keys)
+        self.h_count = [torch.zeros(nb, dtype=torch.int32).pin_memory() for _ in range(2)]
+        self.h_x = [[torch.zeros((capacity, p.K), dtype=torch.float32).pin_memory() for p in self.mf.plans]
+                    for _ in range(2)]
+        self.h_y = [[torch.zeros((capacity, p.M), dtype=torch.float32).pin_memory() for p in self.mf.plans]
+                    for _ in range(2)]
+        self.done = [torch.cuda.Event() for _ in range(2)]
+        self.copies = {"h2d_bytes": 0, "d2h_bytes": 0}
 
     def capture(self) -> None:
-        """Capture one wave: H2D of counts and scenes, the multi-job forward, D2H of images."""
-        # Warm up the exact op sequence eagerly before capturing it.
+        """Capture the multi-job forward (counts, scenes and images stay in device memory)."""
         torch.cuda.synchronize()
         with torch.cuda.stream(self.stream):
-            self._wave_ops()
+            self.mf.enqueue(self.stream)
         self.stream.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=self.stream):
-            self._wave_ops()
+            self.mf.enqueue(self.stream)
         self.graph = g
 
-    def run_wave(self, wave):
-        """wave: list of (bucket key, scene vector).  Returns images in wave order."""
-        slots = []
+    def _pack(self, buf: int, wave):
+        """Group the wave's scenes by bucket and stack each group into pinned staging."""
+        groups = {}
+        for pos, (key, x) in enumerate(wave):
+            groups.setdefault(self.index[key], []).append(pos)
         counts = [0] * len(self.keys)
-        for key, x in wave:
-            j = self.keys.index(key)
-            if counts[j] >= self.capacity:
+        slots = [None] * len(wave)
+        for j, poss in groups.items():
+            if len(poss) > self.capacity:
                 raise ValueError("bucket capacity exceeded")
-            self.h_x[j][counts[j]].copy_(torch.as_tensor(x, dtype=torch.float32))
-            slots.append((j, counts[j]))
-            counts[j] += 1
-        self.h_count.copy_(torch.tensor(counts, dtype=torch.int32))
-        # Replay on the capture stream and wait on that stream: replay() launches
-        # on the current stream, and the pinned outputs are read right after.
+            counts[j] = len(poss)
+            np.stack([np.asarray(wave[p][1], dtype=np.float32).reshape(-1) for p in poss],
+                     out=self.h_x[buf][j][:len(poss)].numpy())
+            for b, p in enumerate(poss):
+                slots[p] = (j, b)
+        self.h_count[buf].copy_(torch.tensor(counts, dtype=torch.int32))
+        return counts, slots
+
+    def _launch(self, buf: int, counts) -> None:
+        mf = self.mf
         with torch.cuda.stream(self.stream):
+            mf.count.copy_(self.h_count[buf], non_blocking=True)
+            for j, c in enumerate(counts):
+                if c:
+                    mf.x[j][:c].copy_(self.h_x[buf][j][:c], non_blocking=True)
+                    self.copies["h2d_bytes"] += c * mf.x[j].shape[1] * 4
             if self.graph is not None:
                 self.graph.replay()
             else:
-                self._wave_ops()
-        self.stream.synchronize()
-        return [self.h_y[j][b].clone() for j, b in slots]
+                mf.enqueue(self.stream)
+            for j, c in enumerate(counts):
+                if c:
+                    self.h_y[buf][j][:c].copy_(mf.y[j][:c], non_blocking=True)
+                    self.copies["d2h_bytes"] += c * mf.y[j].shape[1] * 4
+            self.done[buf].record(self.stream)
+
+    def run_wave(self, wave):
+        """wave: list of (bucket key, scene vector).  Returns images in wave order."""
+        counts, slots = self._pack(0, wave)
+        self._launch(0, counts)
+        self.done[0].synchronize()
+        return [self.h_y[0][j][b].clone() for j, b in slots]
+
+    def run_waves(self, waves):
+        """Serve waves back to back: wave i + 1 is packed on the host while the GPU
+        works on wave i.  Yields (images in wave order, seconds from the start of
+        the wave's packing to its images being back in host memory) per wave."""
+        pending = None
+        for i, wave in enumerate(waves):
+            buf = i & 1
+            t0 = time.perf_counter()
+            counts, slots = self._pack(buf, wave)
+            self._launch(buf, counts)
+            if pending is not None:
+                yield self._collect(*pending)
+            pending = (buf, slots, t0)
+        if pending is not None:
+            yield self._collect(*pending)
+
+    def _collect(self, buf, slots, t0):
+        self.done[buf].synchronize()
+        out = [self.h_y[buf][j][b].clone() for j, b in slots]
+        return out, time.perf_counter() - t0
