@@ -39,13 +39,16 @@
 // Warps: 16, all generators (four per scheduler partition, so each thread
 // may hold 128 registers).  Thread 0 also issues the x tiles' TMA loads, and
 // for each stage the warp that finishes its part last issues the stage's
-// tcgen05.mma (one lane).  An M-tile is an 8 x 16 block of image pixels.
-// Warp g builds columns 4g .. 4g+3 of every 128 x 64 tile for all 128 rows:
-// lane l handles the pixels (l % 8, l / 8 + 4t), t = 0..3, i.e. tile row
-// 32t + l, so a warp's 32 simultaneous loads come from one compact 8 x 4
-// pixel patch.  Warps also drain the TMEM accumulator of rotation g / 4 for
-// rows 32 (g % 4) .. +31 every kChunk k-tiles into a running FP32 sum kept in
-// a third TMEM region (the tensor core's FP32 accumulation is not
+// tcgen05.mma (one lane).  An M-tile is an 8 x 16 block of image pixels, tile
+// row 8 dv + du for pixel (du, dv).  Warp g builds columns 4g .. 4g+3 of
+// every 128 x 64 tile: lane l takes column 4g + l % 4 for the pixels
+// du = l / 4 of all 16 rows dv, so one warp load covers 8 neighbouring pixels
+// x 4 neighbouring columns (columns are sorted by angle within each radial
+// bracket, and neighbouring columns often need the same footprint entry for a
+// pixel: the request touches fewer sectors), with eight rows' loads in flight
+// per lane.  Warps also drain the TMEM accumulator of rotation g / 4 for rows
+// 32 (g % 4) .. +31 every kChunk k-tiles into a running FP32 sum kept in a
+// third TMEM region (the tensor core's FP32 accumulation is not
 // round-to-nearest, so long accumulations drift; the sums are added on the
 // CUDA cores, and keeping them in TMEM leaves the registers to generation).
 // Every wait is bounded; after a timeout each role waits (bounded) for the
@@ -71,9 +74,9 @@ constexpr uint32_t kSumCol = 256;            // running sums: columns 256 .. 256
 constexpr uint32_t kTileBytes = BM * BK * 2;
 constexpr int kTileW = 8, kTileH = 16;       // M-tile: 8 x 16 image pixels
 constexpr int kCols = BK / kWarps;           // columns per generator warp per k-tile
-constexpr int kSlots = BM / 32;              // tile rows per lane
+constexpr int kDepth = 8;                    // rows whose footprint loads a lane keeps in flight
 constexpr int kTabTiles = 4;                 // k-tiles per column table (one generator barrier each)
-static_assert(kTileW * kTileH == BM && kCols == 4 && kSlots == 4 && kWarps == 16, "tile shape");
+static_assert(kTileW * kTileH == BM && kCols == 4 && kWarps == 16 && kTileH % kDepth == 0, "tile shape");
 constexpr int kFixShift = PSFSIM_FRAC_BITS + 1;  // fraction bits of the source coordinates a and b
 
 struct FusedParams {
@@ -354,14 +357,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int n = P.n;
   const uint32_t un = (uint32_t)n;
   const uint32_t nq = (uint32_t)(n + 1);
-  const uint32_t du = (uint32_t)(lane & 7);
-  const uint32_t ndu = (uint32_t)(kTileW - 1) - du;
-  const uint32_t dv0 = (uint32_t)(lane >> 3);
-  // Swizzled shared-memory address of this lane's 8 bytes (4 bf16 columns
-  // 4g..4g+3) in tile row 32t + lane: 16-byte chunk index XOR (row % 8)
-  // inside each 1024-byte group of 8 rows (128-byte swizzle).
-  const uint32_t row_off = (uint32_t)(lane >> 3) * 1024 + (uint32_t)(lane & 7) * 128 +
-                           (((uint32_t)(g >> 1) ^ (uint32_t)(lane & 7)) << 4) + (uint32_t)(g & 1) * 8;
+  // Lane l generates column 4g + (l % 4) for the pixels du = l / 4 of the
+  // tile's 8-pixel rows dv = 0..15 (tile row 8 dv + du): a warp's load then
+  // covers 8 neighbouring pixels x 4 neighbouring columns, and columns next
+  // to each other in the sorted order often need the same footprint entry
+  // for a pixel, so the request touches fewer sectors.
+  const int col = g * kCols + (lane & 3);
+  const uint32_t du = (uint32_t)(lane >> 2);
+  // Swizzled shared-memory address of this lane's bf16 in tile row dv * 8 +
+  // du: 16-byte chunk index XOR (row % 8) inside each 1024-byte group of 8
+  // rows (128-byte swizzle); row group dv adds dv * 1024.
+  const uint32_t row_off = du * 128 + ((((uint32_t)col >> 3) ^ du) << 4) + ((uint32_t)col & 7) * 2;
   uint32_t it = 0, c = 0, tg = 0;
   const ColEntry *cur = ctab[0];
   bool ok = true;
@@ -433,61 +439,52 @@ __global__ void __launch_bounds__(kThreads, 1)
           ptx::tma_load_2d(stage + 2 * kTileBytes, &map_x, kt * BK, 0, &xfull[s]);
           ++x_issued;
         }
-        float y[kSlots][kCols];
-        // Two columns at a time: all eight loads (two columns x four rows) are
-        // in flight before any is used.
-#pragma unroll
-        for (int c2 = 0; c2 < kCols; c2 += 2) {
-          Entry ent[2][kSlots];
-          uint32_t fa[2][kSlots], fb[2][kSlots];
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const ColEntry ce = tab[c2 + h];
-            const unsigned long long abase = ce.C2 * du + (unsigned long long)ce.A0;
-            const unsigned long long bbase = ce.S2 * ndu + (unsigned long long)ce.B0;
-#pragma unroll
-            for (int t = 0; t < kSlots; ++t) {
-              const uint32_t dv = dv0 + 4u * (uint32_t)t;
-              const unsigned long long a = ce.S2 * dv + abase;
-              const unsigned long long b = ce.C2 * dv + bbase;
-              const uint32_t qa = (uint32_t)(a >> kFixShift), pb = (uint32_t)(b >> kFixShift);
-              const bool inside = qa <= un && pb <= un;
-              const uint32_t idx = inside ? ce.off + pb * nq + qa : P.zero_entry;
-              ent[h][t] = load_entry(P.plib + 8 * (size_t)idx);
-              fa[h][t] = (uint32_t)(a >> (kFixShift - 32));
-              fb[h][t] = (uint32_t)(b >> (kFixShift - 32));
-            }
-          }
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const float w0 = tab[c2 + h].w0, w1 = tab[c2 + h].w1;
-#pragma unroll
-            for (int t = 0; t < kSlots; ++t) {
-              float an, af, bn, bf;
-              axis_weights(fa[h][t], an, af);
-              axis_weights(fb[h][t], bn, bf);
-              const uint64_t an2 = f2_pack(an, an), af2 = f2_pack(af, af);
-              const uint64_t r0 = fma2(af2, ent[h][t].t01, mul2(an2, ent[h][t].t00));  // row p, both PSFs
-              const uint64_t r1 = fma2(af2, ent[h][t].t11, mul2(an2, ent[h][t].t10));  // row p + 1
-              const uint64_t v = fma2(f2_pack(bf, bf), r1, mul2(f2_pack(bn, bn), r0));
-              float v0, v1;
-              f2_unpack(v, v0, v1);
-              y[t][c2 + h] = fmaf(w1, v1, w0 * v0);
-            }
-          }
-        }
+        const ColEntry ce = tab[col - g * kCols];
+        const float w0 = ce.w0, w1 = ce.w1;
+        // Source coordinates of pixel (du, dv): one row down adds (S, C).
+        unsigned long long a = ce.C2 * du + (unsigned long long)ce.A0;
+        unsigned long long b = ce.S2 * ((uint32_t)(kTileW - 1) - du) + (unsigned long long)ce.B0;
         uint8_t *st = stage + row_off;
+        // Rolling prefetch: the loads of kDepth rows are in flight while the
+        // earliest is used.
+        Entry ent[kDepth];
+        uint32_t fa[kDepth], fb[kDepth];
+        auto issue = [&](int t) {
+          const uint32_t qa = (uint32_t)(a >> kFixShift), pb = (uint32_t)(b >> kFixShift);
+          const bool inside = qa <= un && pb <= un;
+          const uint32_t idx = inside ? ce.off + pb * nq + qa : P.zero_entry;
+          ent[t % kDepth] = load_entry(P.plib + 8 * (size_t)idx);
+          fa[t % kDepth] = (uint32_t)(a >> (kFixShift - 32));
+          fb[t % kDepth] = (uint32_t)(b >> (kFixShift - 32));
+          a += ce.S2;
+          b += ce.C2;
+        };
+        auto finish = [&](int t) {
+          const int i = t % kDepth;
+          float an, af, bn, bf;
+          axis_weights(fa[i], an, af);
+          axis_weights(fb[i], bn, bf);
+          const uint64_t an2 = f2_pack(an, an), af2 = f2_pack(af, af);
+          const uint64_t r0 = fma2(af2, ent[i].t01, mul2(an2, ent[i].t00));  // row p, both PSFs
+          const uint64_t r1 = fma2(af2, ent[i].t11, mul2(an2, ent[i].t10));  // row p + 1
+          const uint64_t v = fma2(f2_pack(bf, bf), r1, mul2(f2_pack(bn, bn), r0));
+          float v0, v1;
+          f2_unpack(v, v0, v1);
+          const float y = fmaf(w1, v1, w0 * v0);
+          const __nv_bfloat16 hi = __float2bfloat16_rn(y);
+          const __nv_bfloat16 lo = __float2bfloat16_rn(y - __bfloat162float(hi));
+          *reinterpret_cast<__nv_bfloat16 *>(st + t * 1024) = hi;
+          *reinterpret_cast<__nv_bfloat16 *>(st + kTileBytes + t * 1024) = lo;
+        };
 #pragma unroll
-        for (int t = 0; t < kSlots; ++t) {
-          const __nv_bfloat162 h01 = __floats2bfloat162_rn(y[t][0], y[t][1]);
-          const __nv_bfloat162 h23 = __floats2bfloat162_rn(y[t][2], y[t][3]);
-          const __nv_bfloat162 l01 = __floats2bfloat162_rn(y[t][0] - __low2float(h01), y[t][1] - __high2float(h01));
-          const __nv_bfloat162 l23 = __floats2bfloat162_rn(y[t][2] - __low2float(h23), y[t][3] - __high2float(h23));
-          *reinterpret_cast<uint2 *>(st + t * 4096) =
-              make_uint2(*reinterpret_cast<const uint32_t *>(&h01), *reinterpret_cast<const uint32_t *>(&h23));
-          *reinterpret_cast<uint2 *>(st + kTileBytes + t * 4096) =
-              make_uint2(*reinterpret_cast<const uint32_t *>(&l01), *reinterpret_cast<const uint32_t *>(&l23));
+        for (int t = 0; t < kDepth; ++t) issue(t);
+#pragma unroll
+        for (int t = kDepth; t < kTileH; ++t) {
+          finish(t - kDepth);
+          issue(t);
         }
+#pragma unroll
+        for (int t = kTileH - kDepth; t < kTileH; ++t) finish(t);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (lane == 0) {
