@@ -267,11 +267,13 @@ __device__ __forceinline__ ColEntry column_entry(const FusedParams &P, int64_t t
 }
 
 // The two bilinear weights of one axis, in units of 2^-32, from the 32-bit
-// fraction f of a source coordinate: (2^32 - f, f), each converted from the
-// exact integer (relative error 2^-24 however small).
+// fraction f of a source coordinate: (2^32 - f, f), each from its exact
+// integer, so each is accurate relative to itself however small: f converts
+// with one rounding, 2^32 - f as (2^32 - 1 - f) + 1 with two (the + 1 is
+// exact below 2^24 and under half an ulp above).
 __device__ __forceinline__ void axis_weights(uint32_t f, float &w_near, float &w_far) {
   w_far = __uint2float_rn(f);
-  w_near = f ? __uint2float_rn(0u - f) : 4294967296.f;
+  w_near = __uint2float_rn(~f) + 1.0f;
 }
 
 // MMAs of one stage (k-tile kt of chunk [kc, kc1)), issued by the generator
