@@ -28,17 +28,23 @@ def _vp(t: torch.Tensor) -> ctypes.c_void_p:
 
 
 class MultiForward:
-    """Device buffers and the C-ABI job table for one set of plans."""
+    """Scene, image and count buffers and the C-ABI job table for one set of plans.
 
-    def __init__(self, plans: list[Plan], capacity: list[int], tuning=None):
+    The buffers are device memory by default; `x`, `y` and `count` may instead be given, e.g.
+    pinned host tensors, which the kernels then read and write in place through the device's
+    mapping of pinned memory (no staging copies)."""
+
+    def __init__(self, plans: list[Plan], capacity: list[int], tuning=None, x=None, y=None, count=None):
         if not plans or len(plans) > 16:
             raise ValueError("1..16 plans")
         self.lib = B.load()
         self.plans = plans
         dev = plans[0].lib.device
-        self.x = [torch.zeros((c, p.K), dtype=torch.float32, device=dev) for p, c in zip(plans, capacity)]
-        self.y = [torch.zeros((c, p.M), dtype=torch.float32, device=dev) for p, c in zip(plans, capacity)]
-        self.count = torch.zeros(len(plans), dtype=torch.int32, device=dev)
+        self.x = x if x is not None else [torch.zeros((c, p.K), dtype=torch.float32, device=dev)
+                                          for p, c in zip(plans, capacity)]
+        self.y = y if y is not None else [torch.zeros((c, p.M), dtype=torch.float32, device=dev)
+                                          for p, c in zip(plans, capacity)]
+        self.count = count if count is not None else torch.zeros(len(plans), dtype=torch.int32, device=dev)
         jobs = (B.Job * len(plans))()
         for j, (p, c) in enumerate(zip(plans, capacity)):
             jobs[j] = B.Job(p.handle, _vp(self.x[j]), _vp(self.y[j]), c,
@@ -87,93 +93,96 @@ def autotune(mf: MultiForward, chunks=(2, 4, 8), units=(2, 4, 8), stages=(0,), r
 class UnevenServer:
     """Serve waves of scenes of mixed (N, S) through one persistent multi-job launch.
 
-    A wave's scenes are grouped by bucket and stacked, one host copy per bucket,
-    into pinned staging (two sets, so the next wave is packed while the GPU works
-    on this one).  Only the bytes of the scenes present go to the device and only
-    the images written come back (one copy per non-empty bucket each way); the
-    multi-job forward itself, with its device-side counts, is one captured CUDA
-    graph replayed every wave.
+    Scenes, images and per-bucket counts live in pinned host memory that the kernels read and
+    write directly through the device's mapping of pinned memory (over NVLink-C2C on
+    Grace-Blackwell): each scene of a wave is copied once, into the next free slot of its
+    bucket in the staging buffers; the whole wave (the multi-job split, GEMM and reductions,
+    reading only the scenes present and writing only the images of present slots) is one
+    captured CUDA graph per staging set.  Two staging sets let the next wave be packed while the
+    GPU works on this one.
     """
 
     def __init__(self, plans: dict, capacity: int, tuning=None):
         self.keys = list(plans.keys())
         self.index = {k: j for j, k in enumerate(self.keys)}
-        self.mf = MultiForward([plans[k] for k in self.keys], [capacity] * len(self.keys), tuning)
         self.capacity = capacity
-        self.graph = None
-        dev = self.mf.plans[0].lib.device
+        dev = next(iter(plans.values())).lib.device
         self.stream = torch.cuda.Stream(device=dev)
         nb = len(self.keys)
+        pl = [plans[k] for k in self.keys]
         self.h_count = [torch.zeros(nb, dtype=torch.int32).pin_memory() for _ in range(2)]
-        self.h_x = [[torch.zeros((capacity, p.K), dtype=torch.float32).pin_memory() for p in self.mf.plans]
-                    for _ in range(2)]
-        self.h_y = [[torch.zeros((capacity, p.M), dtype=torch.float32).pin_memory() for p in self.mf.plans]
-                    for _ in range(2)]
+        self.h_x = [[torch.zeros((capacity, p.K), dtype=torch.float32).pin_memory() for p in pl] for _ in range(2)]
+        self.h_y = [[torch.zeros((capacity, p.M), dtype=torch.float32).pin_memory() for p in pl] for _ in range(2)]
+        self.sets = [MultiForward(pl, [capacity] * nb, tuning, x=self.h_x[i], y=self.h_y[i], count=self.h_count[i])
+                     for i in range(2)]
+        self.nx = [[t.numpy() for t in hx] for hx in self.h_x]   # numpy views of the staging
+        self.ncount = [t.numpy() for t in self.h_count]
+        self.mf = self.sets[0]
+        self.graphs = [None, None]
         self.done = [torch.cuda.Event() for _ in range(2)]
         self.copies = {"h2d_bytes": 0, "d2h_bytes": 0}
 
+    def set_tuning(self, tuning) -> None:
+        for mf in self.sets:
+            mf.set_tuning(tuning)
+
     def capture(self) -> None:
-        """Capture the multi-job forward (counts, scenes and images stay in device memory)."""
+        """Capture each staging set's whole wave (the multi-job forward on mapped buffers)."""
         torch.cuda.synchronize()
-        with torch.cuda.stream(self.stream):
-            self.mf.enqueue(self.stream)
-        self.stream.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=self.stream):
-            self.mf.enqueue(self.stream)
-        self.graph = g
+        for i, mf in enumerate(self.sets):
+            with torch.cuda.stream(self.stream):
+                mf.enqueue(self.stream)
+            self.stream.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=self.stream):
+                mf.enqueue(self.stream)
+            self.graphs[i] = g
 
     def _pack(self, buf: int, wave):
-        """Group the wave's scenes by bucket and stack each group into pinned staging."""
-        groups = {}
-        for pos, (key, x) in enumerate(wave):
-            groups.setdefault(self.index[key], []).append(pos)
+        """Copy each scene of the wave into the next free slot of its bucket in the staging set."""
         counts = [0] * len(self.keys)
-        slots = [None] * len(wave)
-        for j, poss in groups.items():
-            if len(poss) > self.capacity:
+        slots = []
+        nx = self.nx[buf]
+        for key, x in wave:
+            j = self.index[key]
+            b = counts[j]
+            if b >= self.capacity:
                 raise ValueError("bucket capacity exceeded")
-            counts[j] = len(poss)
-            np.stack([np.asarray(wave[p][1], dtype=np.float32).reshape(-1) for p in poss],
-                     out=self.h_x[buf][j][:len(poss)].numpy())
-            for b, p in enumerate(poss):
-                slots[p] = (j, b)
-        self.h_count[buf].copy_(torch.tensor(counts, dtype=torch.int32))
+            nx[j][b] = x
+            counts[j] = b + 1
+            slots.append((j, b))
+        self.ncount[buf][:] = counts
         return counts, slots
 
     def _launch(self, buf: int, counts) -> None:
-        mf = self.mf
+        # the kernels read exactly the scenes present and write exactly their images, in place
+        for j, c in enumerate(counts):
+            self.copies["h2d_bytes"] += c * self.h_x[buf][j].shape[1] * 4
+            self.copies["d2h_bytes"] += c * self.h_y[buf][j].shape[1] * 4
         with torch.cuda.stream(self.stream):
-            mf.count.copy_(self.h_count[buf], non_blocking=True)
-            for j, c in enumerate(counts):
-                if c:
-                    mf.x[j][:c].copy_(self.h_x[buf][j][:c], non_blocking=True)
-                    self.copies["h2d_bytes"] += c * mf.x[j].shape[1] * 4
-            if self.graph is not None:
-                self.graph.replay()
+            if self.graphs[buf] is not None:
+                self.graphs[buf].replay()
             else:
-                mf.enqueue(self.stream)
-            for j, c in enumerate(counts):
-                if c:
-                    self.h_y[buf][j][:c].copy_(mf.y[j][:c], non_blocking=True)
-                    self.copies["d2h_bytes"] += c * mf.y[j].shape[1] * 4
+                self.sets[buf].enqueue(self.stream)
             self.done[buf].record(self.stream)
 
-    def run_wave(self, wave):
-        """wave: list of (bucket key, scene vector).  Returns images in wave order."""
+    def run_wave(self, wave, copy: bool = True):
+        """wave: list of (bucket key, scene vector).  Returns images in wave order: copies, or
+        (copy=False) views into the staging set, valid until the next wave that uses it."""
         counts, slots = self._pack(0, wave)
         self._launch(0, counts)
         self.done[0].synchronize()
-        return [self.h_y[0][j][b].clone() for j, b in slots]
+        return [self.h_y[0][j][b].clone() if copy else self.h_y[0][j][b] for j, b in slots]
 
     def run_waves(self, waves):
-        """Serve waves back to back: wave i + 1 is packed on the host while the GPU
-        works on wave i.  Yields (images in wave order, seconds from the start of
-        the wave's packing to its images being back in host memory) per wave."""
+        """Serve waves back to back: wave i + 1 is packed on the host while the GPU works on
+        wave i.  Yields (images in wave order, seconds from the start of the wave's packing to
+        its images being in host memory) per wave."""
         pending = None
         for i, wave in enumerate(waves):
             buf = i & 1
             t0 = time.perf_counter()
+            # the staging set of wave i - 1 is still in use; wave i - 2's (this one) is free
             counts, slots = self._pack(buf, wave)
             self._launch(buf, counts)
             if pending is not None:
@@ -184,5 +193,5 @@ class UnevenServer:
 
     def _collect(self, buf, slots, t0):
         self.done[buf].synchronize()
-        out = [self.h_y[buf][j][b].clone() for j, b in slots]
-        return out, time.perf_counter() - t0
+        secs = time.perf_counter() - t0
+        return [self.h_y[buf][j][b].clone() for j, b in slots], secs
