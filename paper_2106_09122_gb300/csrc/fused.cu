@@ -45,14 +45,21 @@
 // du = l / 4 of all 16 rows dv, so one warp load covers 8 neighbouring pixels
 // x 4 neighbouring columns (columns are sorted by angle within each radial
 // bracket, and neighbouring columns often need the same footprint entry for a
-// pixel: the request touches fewer sectors), with eight rows' loads in flight
-// per lane.  Warps also drain the TMEM accumulator of rotation g / 4 for rows
-// 32 (g % 4) .. +31 every kChunk k-tiles into a running FP32 sum kept in a
-// third TMEM region (the tensor core's FP32 accumulation is not
-// round-to-nearest, so long accumulations drift; the sums are added on the
-// CUDA cores, and keeping them in TMEM leaves the registers to generation).
-// Every wait is bounded; after a timeout each role waits (bounded) for the
-// asynchronous work it issued before the CTA releases its memory.
+// pixel: the request touches fewer sectors).  Each lane derives its column's
+// coordinates itself from the plan's angle-sorted geometry, so the warps
+// share no table and meet at no block-wide barrier: stages, accumulators and
+// running sums are handed over through mbarriers only.  A lane keeps four
+// rows' footprint loads in flight, and the stream runs on across the k-tiles
+// of an accumulation chunk: while a k-tile's last rows are finished, the next
+// k-tile's first rows are already loading.  Warps also drain the TMEM
+// accumulator of rotation g / 4 for rows 32 (g % 4) .. +31 every kChunk
+// k-tiles into a running FP32 sum kept in a third TMEM region (the tensor
+// core's FP32 accumulation is not round-to-nearest, so long accumulations
+// drift; the sums are added on the CUDA cores, and keeping them in TMEM leaves
+// the registers to generation).  Every wait is bounded; after a timeout every
+// later wait fails at once, each warp leaves its loop, and each role waits
+// (bounded) for the asynchronous work it issued before the CTA releases its
+// memory.
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
@@ -74,8 +81,7 @@ constexpr uint32_t kSumCol = 256;            // running sums: columns 256 .. 256
 constexpr uint32_t kTileBytes = BM * BK * 2;
 constexpr int kTileW = 8, kTileH = 16;       // M-tile: 8 x 16 image pixels
 constexpr int kCols = BK / kWarps;           // columns per generator warp per k-tile
-constexpr int kDepth = 8;                    // rows whose footprint loads a lane keeps in flight
-constexpr int kTabTiles = 4;                 // k-tiles per column table (one generator barrier each)
+constexpr int kDepth = 4;                    // rows whose footprint loads a lane keeps in flight
 static_assert(kTileW * kTileH == BM && kCols == 4 && kWarps == 16 && kTileH % kDepth == 0, "tile shape");
 constexpr int kFixShift = PSFSIM_FRAC_BITS + 1;  // fraction bits of the source coordinates a and b
 
@@ -85,26 +91,29 @@ struct FusedParams {
   uint32_t stage_bytes;
   uint32_t pair_entries;  // entries per bracket pair, (n + 1)^2
   uint32_t zero_entry;    // index of the all-zero entry after the last pair
-  const ColGeom *geom;
-  const int *order;
+  const ColGeom *gsort;   // geometry of the angle-sorted columns, K0v entries
   const float *plib;      // pair entries, 8 floats each
   float *part;            // [KS][4][B][rows]
   int *status;
   uint64_t wait_ns;
 };
 
-// Per-column constants of one k-tile for the CTA's current M-tile, shared by
-// the generator warps.  Source column (+1) and row (+1) of tile pixel
-// (du, dv), du in [0, 8), dv in [0, 16), in units of 2^-41:
-//     a = A0 + C2 du + S2 dv,   b = B0 + S2 (7 - du) + C2 dv.
-struct __align__(16) ColEntry {
-  long long A0, B0;
-  unsigned long long C2, S2;  // cos, sin (both in [0, 1) for the quadrant) in units of 2^-41
-  uint32_t off;               // first pair entry of the column's bracket
-  float w0, w1;               // lerp weights of L[k] and L[k+1], times 2^-64
-  uint32_t pad;
+// A lane's column in the current k-tile: source column (+1) and row (+1) of
+// its pixel (du, dv) in units of 2^-41, advanced one tile row (dv) at a time,
+//     a = A0 + C2 du + S2 dv,   b = B0 + S2 (7 - du) + C2 dv,
+// the steps, the column's first pair entry and its lerp weights (x 2^-64).
+struct LaneCol {
+  unsigned long long a, b, C2, S2;
+  uint32_t off;
+  float w0, w1;
 };
-static_assert(sizeof(ColEntry) == 48, "ColEntry layout");
+
+// Geometry of a sorted column held in registers until it is needed.
+struct GeomRegs {
+  long long C, Sn;
+  int k;
+  float w0, w1;
+};
 
 __device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
   uint64_t r;
@@ -200,6 +209,13 @@ __global__ void fused_xgather(const float *__restrict__ x, int B, int Bp, int N,
   }
 }
 
+// gsort[t] = geom[order[t]]: the geometry in the generators' column order.
+__global__ void sorted_geometry_kernel(const ColGeom *__restrict__ geom, const int *__restrict__ order, int64_t K0v,
+                                       ColGeom *__restrict__ gsort) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < K0v; t += (int64_t)gridDim.x * blockDim.x)
+    gsort[t] = geom[order[t]];
+}
+
 __device__ __forceinline__ void set_abort(volatile int *flag, int *status) {
   *flag = 1;
   atomicExch(status, PSFSIM_ERR_TIMEOUT);
@@ -219,51 +235,45 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volati
   return ok != 0;
 }
 
-// Block-wide barrier that also ANDs a flag across the threads, so every warp
-// leaves the pipeline at the same point after a timeout.
-__device__ __forceinline__ bool gen_barrier_and(bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\t"
-      "setp.ne.u32 p, %1, 0;\n\t"
-      "bar.red.and.pred q, 1, %2, p;\n\t"
-      "selp.u32 %0, 1, 0, q;\n\t}"
-      : "=r"(r)
-      : "r"((uint32_t)v), "r"(kThreads)
-      : "memory");
-  return r != 0;
-}
-
 __device__ __forceinline__ int unit_k0(const FusedParams &P, int ks) { return (int)((int64_t)P.k_tiles * ks / P.KS); }
 
-// Column-table entry of sorted column t for the M-tile whose origin pixel is
-// (p0, q0); padding columns get an origin far outside the library (their
-// footprints are all the zero entry) and zero steps.
-__device__ __forceinline__ ColEntry column_entry(const FusedParams &P, int64_t t, int p0, int q0) {
-  ColEntry e;
-  // Padding: an origin far outside the library (every footprint is the zero
-  // entry) and zero steps.
-  e.A0 = e.B0 = -(1ll << 62);
-  e.C2 = e.S2 = 0ull;
-  e.off = 0u;
-  e.w0 = e.w1 = 0.f;
-  e.pad = 0u;
+// Geometry of sorted column t; padding columns (t >= K0v) get zero steps and
+// weights, and lane_start gives them an origin far outside the library.
+__device__ __forceinline__ GeomRegs load_geom(const FusedParams &P, int64_t t) {
+  GeomRegs g;
+  g.C = g.Sn = 0;
+  g.k = -1;
+  g.w0 = g.w1 = 0.f;
   if (t < P.K0v) {
-    const ColGeom gm = P.geom[P.order[t]];
-    const long long h = P.n - 1;
-    // 2a and 2b in units of 2^-PSFSIM_FRAC_BITS, i.e. a and b in units of
-    // 2^-41; +1 pixel (2^42) for the padded index.
-    // Half a unit of 2^-32 (2^8) rounds the fraction the weights use.
-    const long long base = ((h + 2) << PSFSIM_FRAC_BITS) + (1ll << (kFixShift - 33));
-    e.A0 = base + gm.C * (2ll * q0 - h) + gm.Sn * (2ll * p0 - h);
-    e.B0 = base - gm.Sn * (2ll * (q0 + kTileW - 1) - h) + gm.C * (2ll * p0 - h);
-    e.C2 = (unsigned long long)(2 * gm.C);
-    e.S2 = (unsigned long long)(2 * gm.Sn);
-    e.off = (uint32_t)gm.k * P.pair_entries;
-    e.w0 = gm.w0 * 0x1p-64f;
-    e.w1 = gm.w1 * 0x1p-64f;
+    const ColGeom gm = P.gsort[t];
+    g.C = gm.C;
+    g.Sn = gm.Sn;
+    g.k = gm.k;
+    g.w0 = gm.w0;
+    g.w1 = gm.w1;
   }
-  return e;
+  return g;
+}
+
+// Start of a lane's column for the M-tile whose origin pixel is (p0, q0), at
+// its pixel (du, 0).
+__device__ __forceinline__ void lane_start(const FusedParams &P, const GeomRegs &g, int p0, int q0, uint32_t du,
+                                           LaneCol &L) {
+  const long long h = P.n - 1;
+  // 2a and 2b in units of 2^-PSFSIM_FRAC_BITS, i.e. a and b in units of
+  // 2^-41; +1 pixel (2^42) for the padded index.  Half a unit of 2^-32 (2^8)
+  // rounds the fraction the weights use.
+  const long long base = ((h + 2) << PSFSIM_FRAC_BITS) + (1ll << (kFixShift - 33));
+  const long long A0 = base + g.C * (2ll * q0 - h) + g.Sn * (2ll * p0 - h);
+  const long long B0 = base - g.Sn * (2ll * (q0 + kTileW - 1) - h) + g.C * (2ll * p0 - h);
+  L.C2 = (unsigned long long)(2 * g.C);
+  L.S2 = (unsigned long long)(2 * g.Sn);
+  const bool pad = g.k < 0;
+  L.a = pad ? (unsigned long long)(-(1ll << 62)) : L.C2 * du + (unsigned long long)A0;
+  L.b = pad ? (unsigned long long)(-(1ll << 62)) : L.S2 * ((uint32_t)(kTileW - 1) - du) + (unsigned long long)B0;
+  L.off = pad ? 0u : (uint32_t)g.k * P.pair_entries;
+  L.w0 = g.w0 * 0x1p-64f;
+  L.w1 = g.w1 * 0x1p-64f;
 }
 
 // The two bilinear weights of one axis, in units of 2^-32, from the 32-bit
@@ -320,7 +330,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ int arrivals[kMaxStages];
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
-  __shared__ ColEntry ctab[2][kTabTiles * BK];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint64_t lim = P.wait_ns;
   if (threadIdx.x == 0) {
@@ -370,8 +379,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   // du: 16-byte chunk index XOR (row % 8) inside each 1024-byte group of 8
   // rows (128-byte swizzle); row group dv adds dv * 1024.
   const uint32_t row_off = du * 128 + ((((uint32_t)col >> 3) ^ du) << 4) + ((uint32_t)col & 7) * 2;
-  uint32_t it = 0, c = 0, tg = 0;
-  const ColEntry *cur = ctab[0];
+  uint32_t it = 0, c = 0;
   bool ok = true;
   for (int u = blockIdx.x; u < units; u += gridDim.x) {
     const int ks = u / P.m_tiles, mt = u % P.m_tiles;
@@ -406,34 +414,38 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
       return true;
     };
-    // Every exit from this loop happens right after gen_barrier_and, which
-    // all warps reach the same number of times.
-    bool stop = false;
-    for (int kc = k0; kc < k1 && !stop; kc += kChunk, ++c) {
+    // Warps run independently: the stages, the accumulators and the running
+    // sums are handed over through mbarriers only.  After a timeout every
+    // bounded wait fails at once and each warp leaves for the final drain.
+    for (int kc = k0; kc < k1 && ok; kc += kChunk, ++c) {
       const int kc1 = min(kc + kChunk, k1);
+      // The loads of a chunk run as one stream: while a k-tile's last rows
+      // are finished, the first rows of the next are already being loaded.
+      LaneCol L;
+      lane_start(P, load_geom(P, (int64_t)kc * BK + col), p0, q0, du, L);
+      Entry ent[kDepth];
+      uint32_t fa[kDepth], fb[kDepth];
+      auto issue = [&](int t) {
+        const uint32_t qa = (uint32_t)(L.a >> kFixShift), pb = (uint32_t)(L.b >> kFixShift);
+        const bool inside = qa <= un && pb <= un;
+        const uint32_t idx = inside ? L.off + pb * nq + qa : P.zero_entry;
+        ent[t % kDepth] = load_entry(P.plib + 8 * (size_t)idx);
+        fa[t % kDepth] = (uint32_t)(L.a >> (kFixShift - 32));
+        fb[t % kDepth] = (uint32_t)(L.b >> (kFixShift - 32));
+        L.a += L.S2;
+        L.b += L.C2;
+      };
+#pragma unroll
+      for (int t = 0; t < kDepth; ++t) issue(t);
       for (int kt = kc; kt < kc1; ++kt, ++it) {
-        // Column table for the next kTabTiles k-tiles (double-buffered; one
-        // block-wide barrier per table, which also carries the abort decision).
-        if (((kt - k0) % kTabTiles) == 0) {
-          ColEntry *tab = ctab[tg & 1];
-          for (int e = threadIdx.x; e < kTabTiles * BK; e += kThreads) {
-            const int64_t t = (int64_t)kt * BK + e;
-            tab[e] = (kt + e / BK < k1) ? column_entry(P, t, p0, q0) : column_entry(P, P.K0v, p0, q0);
-          }
-          if (!gen_barrier_and(ok)) {
-            stop = true;
-            break;
-          }
-          cur = tab;
-          ++tg;
-        }
-        if (!ok) continue;  // after a timeout: no more work until the next barrier exits
-        const ColEntry *tab = cur + ((kt - k0) % kTabTiles) * BK + g * kCols;
+        const bool more = kt + 1 < kc1;
+        GeomRegs gn;
+        if (more) gn = load_geom(P, (int64_t)(kt + 1) * BK + col);
         const int s = (int)(it % P.stages);
         const uint32_t par = (it / P.stages) & 1;
         if (!warp_wait(&empty[s], par ^ 1, &abort_flag, P.status, lim)) {
           ok = false;
-          continue;
+          break;
         }
         uint8_t *stage = smem + (size_t)s * P.stage_bytes;
         if (producer) {
@@ -441,26 +453,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           ptx::tma_load_2d(stage + 2 * kTileBytes, &map_x, kt * BK, 0, &xfull[s]);
           ++x_issued;
         }
-        const ColEntry ce = tab[col - g * kCols];
-        const float w0 = ce.w0, w1 = ce.w1;
-        // Source coordinates of pixel (du, dv): one row down adds (S, C).
-        unsigned long long a = ce.C2 * du + (unsigned long long)ce.A0;
-        unsigned long long b = ce.S2 * ((uint32_t)(kTileW - 1) - du) + (unsigned long long)ce.B0;
+        const float w0 = L.w0, w1 = L.w1;
         uint8_t *st = stage + row_off;
-        // Rolling prefetch: the loads of kDepth rows are in flight while the
-        // earliest is used.
-        Entry ent[kDepth];
-        uint32_t fa[kDepth], fb[kDepth];
-        auto issue = [&](int t) {
-          const uint32_t qa = (uint32_t)(a >> kFixShift), pb = (uint32_t)(b >> kFixShift);
-          const bool inside = qa <= un && pb <= un;
-          const uint32_t idx = inside ? ce.off + pb * nq + qa : P.zero_entry;
-          ent[t % kDepth] = load_entry(P.plib + 8 * (size_t)idx);
-          fa[t % kDepth] = (uint32_t)(a >> (kFixShift - 32));
-          fb[t % kDepth] = (uint32_t)(b >> (kFixShift - 32));
-          a += ce.S2;
-          b += ce.C2;
-        };
         auto finish = [&](int t) {
           const int i = t % kDepth;
           float an, af, bn, bf;
@@ -479,14 +473,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           *reinterpret_cast<__nv_bfloat16 *>(st + kTileBytes + t * 1024) = lo;
         };
 #pragma unroll
-        for (int t = 0; t < kDepth; ++t) issue(t);
-#pragma unroll
-        for (int t = kDepth; t < kTileH; ++t) {
-          finish(t - kDepth);
-          issue(t);
+        for (int t = 0; t < kTileH; ++t) {
+          // Rows t + kDepth >= kTileH belong to the next k-tile's column.
+          if (t == kTileH - kDepth && more) lane_start(P, gn, p0, q0, du, L);
+          finish(t);
+          if (t + kDepth < kTileH || more) issue(t + kDepth);
         }
-#pragma unroll
-        for (int t = kTileH - kDepth; t < kTileH; ++t) finish(t);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (lane == 0) {
@@ -500,11 +492,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         __syncwarp();
       }
-      if (!stop && ok && kc > k0 && !drain(c - 1)) ok = false;
+      if (ok && kc > k0 && !drain(c - 1)) ok = false;
     }
-    if (stop) break;
     if (ok && !drain(c - 1)) ok = false;
-    if (!ok) continue;  // the next unit's first barrier takes every warp out
+    if (!ok) break;  // the next unit's first barrier takes every warp out
     // This lane drains tile row 32 quarter + lane: pixel (l % 8, l / 8 + 4 quarter).
     // The TMEM loads are warp-collective, so every lane takes part; only
     // lanes whose pixel lies inside the image store.
@@ -615,6 +606,11 @@ int64_t psfsim_pair_library_bytes(int n, int n_r) { return ((int64_t)(n_r - 1) *
 cudaError_t psfsim_launch_pair_library(psfsim_plan *h, cudaStream_t st) {
   pair_library_kernel<<<h->num_sms * 4, 256, 0, st>>>(h->d_lib, h->n, h->n_r,
                                                       reinterpret_cast<float *>(h->ws + h->plib_off));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || h->K_valid < 1) return e;
+  sorted_geometry_kernel<<<h->num_sms, 256, 0, st>>>(reinterpret_cast<const ColGeom *>(h->ws + h->geom_off),
+                                                     reinterpret_cast<const int *>(h->ws + h->order_off), h->K_valid,
+                                                     reinterpret_cast<ColGeom *>(h->ws + h->gsort_off));
   return cudaGetLastError();
 }
 
@@ -656,8 +652,7 @@ cudaError_t psfsim_launch_forward_fused(const psfsim_plan *h, const float *x, in
     P.stage_bytes = f.stage_bytes;
     P.pair_entries = (uint32_t)((h->n + 1) * (h->n + 1));
     P.zero_entry = (uint32_t)(h->n_r - 1) * P.pair_entries;
-    P.geom = reinterpret_cast<const ColGeom *>(h->ws + h->geom_off);
-    P.order = order;
+    P.gsort = reinterpret_cast<const ColGeom *>(h->ws + h->gsort_off);
     P.plib = reinterpret_cast<const float *>(h->ws + h->plib_off);
     P.part = part;
     P.status = status;
