@@ -360,8 +360,8 @@ WsLayout psfsim_layout(int n, int64_t K, int storage, int n_r) {
   // FUSED keeps the library as pair entries (both PSFs of a radial bracket,
   // each pixel's 2 x 2 bilinear footprint tap by tap, 32 bytes)
   L.plib_off = storage == PSFSIM_FUSED ? take(psfsim_pair_library_bytes(n, n_r)) : -1;
-  // ... and the column geometry in the generators' (angle-sorted) order.
-  L.gsort_off = storage == PSFSIM_FUSED ? take(K * (int64_t)sizeof(ColGeom)) : -1;
+  // ... and the generators' column table.
+  L.cols_off = storage == PSFSIM_FUSED ? take(psfsim_fused_columns_bytes(K)) : -1;
   L.total = off;
   (void)n_r;
   return L;

@@ -45,10 +45,11 @@
 // du = l / 4 of all 16 rows dv, so one warp load covers 8 neighbouring pixels
 // x 4 neighbouring columns (columns are sorted by angle within each radial
 // bracket, and neighbouring columns often need the same footprint entry for a
-// pixel: the request touches fewer sectors).  Each lane derives its column's
-// coordinates itself from the plan's angle-sorted geometry, so the warps
-// share no table and meet at no block-wide barrier: stages, accumulators and
-// running sums are handed over through mbarriers only.  A lane keeps four
+// pixel: the request touches fewer sectors).  Each lane starts its column
+// itself from the plan's column table (origin terms, steps and weights of
+// every column in the angle-sorted order, prepared at build time), so the
+// warps share no table and meet at no block-wide barrier: stages,
+// accumulators and running sums are handed over through mbarriers only.  A lane keeps four
 // rows' footprint loads in flight, and the stream runs on across the k-tiles
 // of an accumulation chunk: while a k-tile's last rows are finished, the next
 // k-tile's first rows are already loading.  Warps also drain the TMEM
@@ -72,7 +73,7 @@ constexpr int BM = 128;
 constexpr int BK = 64;
 constexpr int kWarps = 16;                   // every warp generates; see the file comment for roles
 constexpr int kThreads = kWarps * 32;
-constexpr int kMaxStages = 2;
+constexpr int kStages = 2;
 constexpr int kChunk = 5;                    // k-tiles per accumulation: 5 x 4 x 3 = 60 MMAs
 constexpr int kMaxBp = 32;
 constexpr uint32_t kTmemCols = 512;
@@ -85,33 +86,43 @@ constexpr int kDepth = 4;                    // rows whose footprint loads a lan
 static_assert(kTileW * kTileH == BM && kCols == 4 && kWarps == 16 && kTileH % kDepth == 0, "tile shape");
 constexpr int kFixShift = PSFSIM_FRAC_BITS + 1;  // fraction bits of the source coordinates a and b
 
+// One column of the generators' (angle-sorted) order, prepared at build
+// time.  With X = q0 + du and Y = p0 + dv for tile pixel (du, dv) of the
+// M-tile whose origin pixel is (p0, q0), the source column (+1) and row (+1)
+// in units of 2^-41 are
+//     a = A00 + C2 X + S2 Y,   b = B00 - S2 X + C2 Y
+// (Eq. 2-3's rotation about the library centre (n-1)/2, in fixed point; the
+// half unit of 2^-32 that rounds the weights' fraction is folded into A00
+// and B00).  Padding columns have an origin far outside the library, zero
+// steps and zero weights.
+struct __align__(16) FusedCol {
+  long long A00, B00;
+  unsigned long long C2, S2;  // cos, sin (both in [0, 1) for the quadrant) in units of 2^-41
+  uint32_t off;               // first pair entry of the column's bracket
+  float w0, w1;               // lerp weights of L[k] and L[k+1], times 2^-64
+  uint32_t pad;
+};
+static_assert(sizeof(FusedCol) == 48, "FusedCol layout");
+
 struct FusedParams {
-  int n, N, Bp, B, KS, m_tiles, k_tiles, stages, tiles_q;
+  int n, N, Bp, B, KS, m_tiles, k_tiles, tiles_q;
   int64_t M, rows, K0v;
   uint32_t stage_bytes;
   uint32_t pair_entries;  // entries per bracket pair, (n + 1)^2
   uint32_t zero_entry;    // index of the all-zero entry after the last pair
-  const ColGeom *gsort;   // geometry of the angle-sorted columns, K0v entries
+  const FusedCol *cols;   // the angle-sorted columns, padded to whole k-tiles
   const float *plib;      // pair entries, 8 floats each
   float *part;            // [KS][4][B][rows]
   int *status;
   uint64_t wait_ns;
 };
 
-// A lane's column in the current k-tile: source column (+1) and row (+1) of
-// its pixel (du, dv) in units of 2^-41, advanced one tile row (dv) at a time,
-//     a = A0 + C2 du + S2 dv,   b = B0 + S2 (7 - du) + C2 dv,
-// the steps, the column's first pair entry and its lerp weights (x 2^-64).
+// A lane's column in the current k-tile: the source coordinates a and b of
+// its pixel in the current tile row (advanced one row, dv, at a time), the
+// steps, the column's first pair entry and its lerp weights (x 2^-64).
 struct LaneCol {
   unsigned long long a, b, C2, S2;
   uint32_t off;
-  float w0, w1;
-};
-
-// Geometry of a sorted column held in registers until it is needed.
-struct GeomRegs {
-  long long C, Sn;
-  int k;
   float w0, w1;
 };
 
@@ -209,11 +220,37 @@ __global__ void fused_xgather(const float *__restrict__ x, int B, int Bp, int N,
   }
 }
 
-// gsort[t] = geom[order[t]]: the geometry in the generators' column order.
-__global__ void sorted_geometry_kernel(const ColGeom *__restrict__ geom, const int *__restrict__ order, int64_t K0v,
-                                       ColGeom *__restrict__ gsort) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < K0v; t += (int64_t)gridDim.x * blockDim.x)
-    gsort[t] = geom[order[t]];
+// cols[t] from the geometry of column order[t] (the generators' order);
+// entries from K0v up to the next whole k-tile are padding.
+__global__ void fused_columns_kernel(const ColGeom *__restrict__ geom, const int *__restrict__ order, int n,
+                                     uint32_t pair_entries, int64_t K0v, int64_t Kpad, FusedCol *__restrict__ cols) {
+  const long long h = n - 1;
+  // 2a and 2b in units of 2^-PSFSIM_FRAC_BITS, i.e. a and b in units of
+  // 2^-41; +1 pixel (2^42) for the padded index; half a unit of 2^-32 (2^8)
+  // rounds the fraction the weights use.
+  const long long base = ((h + 2) << PSFSIM_FRAC_BITS) + (1ll << (kFixShift - 33));
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < Kpad; t += (int64_t)gridDim.x * blockDim.x) {
+    FusedCol c;
+    c.A00 = c.B00 = -(1ll << 62);
+    c.C2 = c.S2 = 0ull;
+    c.off = 0u;
+    c.w0 = c.w1 = 0.f;
+    c.pad = 0u;
+    if (t < K0v) {
+      const ColGeom gm = geom[order[t]];
+      // Tile pixel (du, dv) of the M-tile at (p0, q0) is image pixel
+      // (p0 + dv, q0 + du); its source coordinates are
+      //     a = base + C (2 X - h) + Sn (2 Y - h),  b = base - Sn (2 X - h) + C (2 Y - h).
+      c.A00 = base - h * (gm.C + gm.Sn);
+      c.B00 = base + h * (gm.Sn - gm.C);
+      c.C2 = (unsigned long long)(2 * gm.C);
+      c.S2 = (unsigned long long)(2 * gm.Sn);
+      c.off = (uint32_t)gm.k * pair_entries;
+      c.w0 = gm.w0 * 0x1p-64f;
+      c.w1 = gm.w1 * 0x1p-64f;
+    }
+    cols[t] = c;
+  }
 }
 
 __device__ __forceinline__ void set_abort(volatile int *flag, int *status) {
@@ -235,45 +272,33 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volati
   return ok != 0;
 }
 
-__device__ __forceinline__ int unit_k0(const FusedParams &P, int ks) { return (int)((int64_t)P.k_tiles * ks / P.KS); }
-
-// Geometry of sorted column t; padding columns (t >= K0v) get zero steps and
-// weights, and lane_start gives them an origin far outside the library.
-__device__ __forceinline__ GeomRegs load_geom(const FusedParams &P, int64_t t) {
-  GeomRegs g;
-  g.C = g.Sn = 0;
-  g.k = -1;
-  g.w0 = g.w1 = 0.f;
-  if (t < P.K0v) {
-    const ColGeom gm = P.gsort[t];
-    g.C = gm.C;
-    g.Sn = gm.Sn;
-    g.k = gm.k;
-    g.w0 = gm.w0;
-    g.w1 = gm.w1;
+// Bounded wait by lane 0 alone: the warp's later accesses are ordered after
+// its acquire by __syncwarp.
+__device__ __forceinline__ bool warp_wait_lane0(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *status,
+                                                uint64_t lim) {
+  int ok = 0;
+  if ((threadIdx.x & 31) == 0) {
+    ok = !*abort_flag && ptx::mbar_wait_bounded(bar, parity, lim);
+    if (!ok) set_abort(abort_flag, status);
   }
-  return g;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();
+  return ok != 0;
 }
+
+__device__ __forceinline__ int unit_k0(const FusedParams &P, int ks) { return (int)((int64_t)P.k_tiles * ks / P.KS); }
 
 // Start of a lane's column for the M-tile whose origin pixel is (p0, q0), at
 // its pixel (du, 0).
-__device__ __forceinline__ void lane_start(const FusedParams &P, const GeomRegs &g, int p0, int q0, uint32_t du,
-                                           LaneCol &L) {
-  const long long h = P.n - 1;
-  // 2a and 2b in units of 2^-PSFSIM_FRAC_BITS, i.e. a and b in units of
-  // 2^-41; +1 pixel (2^42) for the padded index.  Half a unit of 2^-32 (2^8)
-  // rounds the fraction the weights use.
-  const long long base = ((h + 2) << PSFSIM_FRAC_BITS) + (1ll << (kFixShift - 33));
-  const long long A0 = base + g.C * (2ll * q0 - h) + g.Sn * (2ll * p0 - h);
-  const long long B0 = base - g.Sn * (2ll * (q0 + kTileW - 1) - h) + g.C * (2ll * p0 - h);
-  L.C2 = (unsigned long long)(2 * g.C);
-  L.S2 = (unsigned long long)(2 * g.Sn);
-  const bool pad = g.k < 0;
-  L.a = pad ? (unsigned long long)(-(1ll << 62)) : L.C2 * du + (unsigned long long)A0;
-  L.b = pad ? (unsigned long long)(-(1ll << 62)) : L.S2 * ((uint32_t)(kTileW - 1) - du) + (unsigned long long)B0;
-  L.off = pad ? 0u : (uint32_t)g.k * P.pair_entries;
-  L.w0 = g.w0 * 0x1p-64f;
-  L.w1 = g.w1 * 0x1p-64f;
+__device__ __forceinline__ void lane_start(const FusedCol &c, int p0, int q0, uint32_t du, LaneCol &L) {
+  const uint32_t X = (uint32_t)q0 + du, Y = (uint32_t)p0;
+  L.C2 = c.C2;
+  L.S2 = c.S2;
+  L.a = (unsigned long long)c.A00 + c.C2 * X + c.S2 * Y;
+  L.b = (unsigned long long)c.B00 - c.S2 * X + c.C2 * Y;
+  L.off = c.off;
+  L.w0 = c.w0;
+  L.w1 = c.w1;
 }
 
 // The two bilinear weights of one axis, in units of 2^-32, from the 32-bit
@@ -325,15 +350,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     fused_kernel(const __grid_constant__ CUtensorMap map_x, const FusedParams P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t xfull[kMaxStages], gfull[kMaxStages], empty[kMaxStages], tfull[2], tempty[2];
+  __shared__ __align__(8) uint64_t xfull[kStages], gfull[kStages], empty[kStages], tfull[2], tempty[2];
   __shared__ __align__(8) uint64_t drain_bar;
-  __shared__ int arrivals[kMaxStages];
+  __shared__ int arrivals[kStages];
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint64_t lim = P.wait_ns;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < P.stages; ++s) {
+    for (int s = 0; s < kStages; ++s) {
       ptx::mbar_init(&xfull[s], 1);
       ptx::mbar_init(&gfull[s], kWarps);
       ptx::mbar_init(&empty[s], 1);
@@ -422,7 +447,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // The loads of a chunk run as one stream: while a k-tile's last rows
       // are finished, the first rows of the next are already being loaded.
       LaneCol L;
-      lane_start(P, load_geom(P, (int64_t)kc * BK + col), p0, q0, du, L);
+      lane_start(P.cols[(int64_t)kc * BK + col], p0, q0, du, L);
       Entry ent[kDepth];
       uint32_t fa[kDepth], fb[kDepth];
       auto issue = [&](int t) {
@@ -439,11 +464,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int t = 0; t < kDepth; ++t) issue(t);
       for (int kt = kc; kt < kc1; ++kt, ++it) {
         const bool more = kt + 1 < kc1;
-        GeomRegs gn;
-        if (more) gn = load_geom(P, (int64_t)(kt + 1) * BK + col);
-        const int s = (int)(it % P.stages);
-        const uint32_t par = (it / P.stages) & 1;
-        if (!warp_wait(&empty[s], par ^ 1, &abort_flag, P.status, lim)) {
+        // The next column's entry, read where its first row is issued.
+        const FusedCol *next_col = P.cols + ((int64_t)(kt + 1) * BK + col);
+        FusedCol cn;
+        const int s = (int)(it % kStages);
+        const uint32_t par = (it / kStages) & 1;
+        if (!warp_wait_lane0(&empty[s], par ^ 1, &abort_flag, P.status, lim)) {
           ok = false;
           break;
         }
@@ -475,7 +501,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int t = 0; t < kTileH; ++t) {
           // Rows t + kDepth >= kTileH belong to the next k-tile's column.
-          if (t == kTileH - kDepth && more) lane_start(P, gn, p0, q0, du, L);
+          if (t == kTileH - kDepth && more) cn = *next_col;
+          if (t == kTileH - kDepth && more) lane_start(cn, p0, q0, du, L);
           finish(t);
           if (t + kDepth < kTileH || more) issue(t + kDepth);
         }
@@ -528,8 +555,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   // x the producer issued land.
   if (lane == 0) ptx::mma_commit(&drain_bar);
   if (producer) {
-    for (uint32_t i = x_issued > (uint32_t)P.stages ? x_issued - (uint32_t)P.stages : 0u; i < x_issued; ++i)
-      if (!ptx::mbar_wait_bounded(&xfull[i % P.stages], (i / P.stages) & 1, lim)) set_abort(&abort_flag, P.status);
+    for (uint32_t i = x_issued > (uint32_t)kStages ? x_issued - (uint32_t)kStages : 0u; i < x_issued; ++i)
+      if (!ptx::mbar_wait_bounded(&xfull[i % kStages], (i / kStages) & 1, lim)) set_abort(&abort_flag, P.status);
   }
   if (lane == 0 && !ptx::mbar_wait_bounded(&drain_bar, 0, lim)) set_abort(&abort_flag, P.status);
   __syncthreads();
@@ -561,7 +588,7 @@ bool encode_x_map(CUtensorMap *map, const void *base, uint64_t inner, uint64_t o
 }
 
 struct FusedPlanInfo {
-  int Bp, KS, m_tiles, k_tiles, stages, tiles_q;
+  int Bp, KS, m_tiles, k_tiles, tiles_q;
   int64_t rows, ldx;
   uint32_t stage_bytes;
   size_t smem, xs_bytes, part_bytes;
@@ -592,8 +619,7 @@ FusedPlanInfo fused_info(const psfsim_plan *h, int Bc) {
   // Two stages: a stage's MMAs take a fraction of the time its generation
   // does, and the shared memory a third stage would take is worth more as
   // L1 cache for the library footprints.
-  f.stages = 2;
-  f.smem = (size_t)f.stages * f.stage_bytes + 1024;
+  f.smem = (size_t)kStages * f.stage_bytes + 1024;
   f.xs_bytes = (size_t)psfsim_round_up(8ll * f.Bp * f.ldx * 2, 256);
   f.part_bytes = (size_t)4 * f.KS * Bc * f.rows * 4;
   return f;
@@ -603,14 +629,19 @@ FusedPlanInfo fused_info(const psfsim_plan *h, int Bc) {
 
 int64_t psfsim_pair_library_bytes(int n, int n_r) { return ((int64_t)(n_r - 1) * (n + 1) * (n + 1) + 1) * 32; }
 
+int64_t psfsim_fused_columns_bytes(int64_t K) { return (psfsim_round_up(K, BK) + BK) * (int64_t)sizeof(FusedCol); }
+
 cudaError_t psfsim_launch_pair_library(psfsim_plan *h, cudaStream_t st) {
   pair_library_kernel<<<h->num_sms * 4, 256, 0, st>>>(h->d_lib, h->n, h->n_r,
                                                       reinterpret_cast<float *>(h->ws + h->plib_off));
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || h->K_valid < 1) return e;
-  sorted_geometry_kernel<<<h->num_sms, 256, 0, st>>>(reinterpret_cast<const ColGeom *>(h->ws + h->geom_off),
-                                                     reinterpret_cast<const int *>(h->ws + h->order_off), h->K_valid,
-                                                     reinterpret_cast<ColGeom *>(h->ws + h->gsort_off));
+  if (e != cudaSuccess) return e;
+  // At least one whole k-tile of entries: a plan with no column inside the
+  // last radius still runs one k-tile of padding.
+  fused_columns_kernel<<<h->num_sms, 256, 0, st>>>(
+      reinterpret_cast<const ColGeom *>(h->ws + h->geom_off), reinterpret_cast<const int *>(h->ws + h->order_off), h->n,
+      (uint32_t)((h->n + 1) * (h->n + 1)), h->K_valid, psfsim_round_up(h->K_valid > 0 ? h->K_valid : 1, BK),
+      reinterpret_cast<FusedCol *>(h->ws + h->cols_off));
   return cudaGetLastError();
 }
 
@@ -645,14 +676,13 @@ cudaError_t psfsim_launch_forward_fused(const psfsim_plan *h, const float *x, in
     P.m_tiles = f.m_tiles;
     P.tiles_q = f.tiles_q;
     P.k_tiles = f.k_tiles;
-    P.stages = f.stages;
     P.M = h->M;
     P.rows = f.rows;
     P.K0v = h->K_valid;
     P.stage_bytes = f.stage_bytes;
     P.pair_entries = (uint32_t)((h->n + 1) * (h->n + 1));
     P.zero_entry = (uint32_t)(h->n_r - 1) * P.pair_entries;
-    P.gsort = reinterpret_cast<const ColGeom *>(h->ws + h->gsort_off);
+    P.cols = reinterpret_cast<const FusedCol *>(h->ws + h->cols_off);
     P.plib = reinterpret_cast<const float *>(h->ws + h->plib_off);
     P.part = part;
     P.status = status;
