@@ -116,6 +116,7 @@ class UnevenServer:
         self.sets = [MultiForward(pl, [capacity] * nb, tuning, x=self.h_x[i], y=self.h_y[i], count=self.h_count[i])
                      for i in range(2)]
         self.nx = [[t.numpy() for t in hx] for hx in self.h_x]   # numpy views of the staging
+        self.ny = [[t.numpy() for t in hy] for hy in self.h_y]
         self.ncount = [t.numpy() for t in self.h_count]
         self.mf = self.sets[0]
         self.graphs = [None, None]
@@ -166,13 +167,23 @@ class UnevenServer:
                 self.sets[buf].enqueue(self.stream)
             self.done[buf].record(self.stream)
 
+    def _images(self, buf: int, counts, slots, copy: bool):
+        """The wave's images in wave order.  copy=True: each bucket's present images leave the
+        staging set in one block copy, and the images are views of those blocks; copy=False:
+        views into the staging set, valid until the next wave that uses it."""
+        if not copy:
+            return [self.h_y[buf][j][b] for j, b in slots]
+        ny = self.ny[buf]
+        blocks = {j: torch.from_numpy(ny[j][:c].copy()) for j, c in enumerate(counts) if c}
+        return [blocks[j][b] for j, b in slots]
+
     def run_wave(self, wave, copy: bool = True):
-        """wave: list of (bucket key, scene vector).  Returns images in wave order: copies, or
-        (copy=False) views into the staging set, valid until the next wave that uses it."""
+        """wave: list of (bucket key, scene vector).  Returns the images in wave order (see
+        _images for copy)."""
         counts, slots = self._pack(0, wave)
         self._launch(0, counts)
         self.done[0].synchronize()
-        return [self.h_y[0][j][b].clone() if copy else self.h_y[0][j][b] for j, b in slots]
+        return self._images(0, counts, slots, copy)
 
     def run_waves(self, waves):
         """Serve waves back to back: wave i + 1 is packed on the host while the GPU works on
@@ -187,11 +198,11 @@ class UnevenServer:
             self._launch(buf, counts)
             if pending is not None:
                 yield self._collect(*pending)
-            pending = (buf, slots, t0)
+            pending = (buf, counts, slots, t0)
         if pending is not None:
             yield self._collect(*pending)
 
-    def _collect(self, buf, slots, t0):
+    def _collect(self, buf, counts, slots, t0):
         self.done[buf].synchronize()
-        secs = time.perf_counter() - t0
-        return [self.h_y[buf][j][b].clone() for j, b in slots], secs
+        images = self._images(buf, counts, slots, True)
+        return images, time.perf_counter() - t0
