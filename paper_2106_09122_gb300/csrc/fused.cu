@@ -39,19 +39,23 @@
 // Warps: 16, all generators (four per scheduler partition, so each thread
 // may hold 128 registers).  Thread 0 also issues the x tiles' TMA loads, and
 // for each stage the warp that finishes its part last issues the stage's
-// tcgen05.mma (one lane).  An M-tile is an 8 x 16 block of image pixels, tile
-// row 8 dv + du for pixel (du, dv).  Warp g builds columns 4g .. 4g+3 of
-// every 128 x 64 tile: lane l takes column 4g + l % 4 for the pixels
-// du = l / 4 of all 16 rows dv, so one warp load covers 8 neighbouring pixels
-// x 4 neighbouring columns (columns are sorted by angle within each radial
-// bracket, and neighbouring columns often need the same footprint entry for a
-// pixel: the request touches fewer sectors).  Each lane starts its column
-// itself from the plan's column table (origin terms, steps and weights of
-// every column in the angle-sorted order, prepared at build time), so the
-// warps share no table and meet at no block-wide barrier: stages,
-// accumulators and running sums are handed over through mbarriers only.  A lane keeps four
-// rows' footprint loads in flight, and the stream runs on across the k-tiles
-// of an accumulation chunk: while a k-tile's last rows are finished, the next
+// tcgen05.mma (one lane).  An M-tile is an 8 x 16 block of image pixels.
+// Warp g builds columns 4g .. 4g+3 of every 128 x 64 tile: lane l takes
+// column 4g + l % 4 for the pixels du = l / 4 of all 16 rows dv, so one warp
+// load covers 8 neighbouring pixels x 4 neighbouring columns (columns are
+// sorted by angle within each radial bracket, and neighbouring columns often
+// need the same footprint entry for a pixel: the request touches fewer
+// sectors).  The A tiles are M-major (the MMA's transposed-A form), with tile
+// row 16 sigma(du) + dv for pixel (du, dv): a lane's 16 values of a k-tile
+// are two runs of 8 contiguous bf16, written as 16-byte stores after pairs of
+// rows are rounded together, and sigma spreads each 8-lane group's stores
+// over 8 bank groups.  Each lane starts its column itself from the plan's
+// column table (origin terms, steps and weights of every column in the
+// angle-sorted order, prepared at build time), so the warps share no table
+// and meet at no block-wide barrier: stages, accumulators and running sums
+// are handed over through mbarriers only.  A lane keeps four rows' footprint
+// loads in flight, and the stream runs on across the k-tiles of an
+// accumulation chunk: while a k-tile's last rows are finished, the next
 // k-tile's first rows are already loading.  Warps also drain the TMEM
 // accumulator of rotation g / 4 for rows 32 (g % 4) .. +31 every kChunk
 // k-tiles into a running FP32 sum kept in a third TMEM region (the tensor
@@ -311,6 +315,29 @@ __device__ __forceinline__ void axis_weights(uint32_t f, float &w_near, float &w
   w_near = __uint2float_rn(~f) + 1.0f;
 }
 
+// The A tiles (hi, lo) are M-major: K groups of 8 columns, each two 1024-byte
+// swizzle atoms of 64 tile rows (128-byte swizzle), the atoms of a group 1024
+// bytes apart (leading byte offset), the groups 2048 bytes apart (stride byte
+// offset).  The descriptor's other fields are those of the K-major one.
+constexpr uint32_t kAtomMN = 1024, kGroupK = 2048;
+
+__device__ __forceinline__ uint64_t smem_desc_mn_sw128(const void *tile) {
+  const uint64_t addr = ptx::smem_u32(tile);
+  uint64_t d = 0;
+  d |= (addr & 0x3FFFFull) >> 4;
+  d |= (uint64_t)(kAtomMN >> 4) << 16;
+  d |= (uint64_t)(kGroupK >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Tile-row block of pixel column du: rows 16 sigma(du) .. +15 (sigma swaps
+// bits 0 and 1), so that the two pixels of each 8-lane group (du = 2i, 2i + 1)
+// have rows 32 apart modulo 64 and their 16-byte stores meet 8 different
+// 16-byte bank groups.  sigma is its own inverse.
+__host__ __device__ constexpr uint32_t sigma(uint32_t du) { return (du & 4u) | ((du & 1u) << 1) | ((du & 2u) >> 1); }
+
 // MMAs of one stage (k-tile kt of chunk [kc, kc1)), issued by the generator
 // lane whose warp finished the stage last: wait for all generators and for the
 // x tile, and (first k-tile of a chunk) for the accumulator to be drained;
@@ -328,19 +355,20 @@ __device__ __forceinline__ void issue_stage_mmas(const FusedParams &P, uint8_t *
     return;
   }
   ptx::tc_fence_after();
-  const uint32_t idesc = ptx::idesc_bf16_f32(BM, 4 * P.Bp);
+  const uint32_t idesc = ptx::idesc_bf16_f32(BM, 4 * P.Bp) | (1u << 15);  // A is M-major
   const uint32_t x2_off = (uint32_t)(4 * P.Bp) * 128;  // x2 rows follow the 4Bp rows of x1
-  const uint64_t dh = ptx::smem_desc_sw128(stage);
-  const uint64_t dl = ptx::smem_desc_sw128(stage + kTileBytes);
+  const uint64_t dh = smem_desc_mn_sw128(stage);
+  const uint64_t dl = smem_desc_mn_sw128(stage + kTileBytes);
   const uint64_t dx1 = ptx::smem_desc_sw128(stage + 2 * kTileBytes);
   const uint64_t dx2 = ptx::smem_desc_sw128(stage + 2 * kTileBytes + x2_off);
   const uint32_t d_tmem = tbase + acc * kAccStride;
 #pragma unroll
   for (int kk = 0; kk < BK / 16; ++kk) {
-    const uint64_t adv = (uint64_t)(kk * 32) >> 4;
-    ptx::mma_bf16(d_tmem, dh + adv, dx1 + adv, idesc, (!first_kt || kk > 0) ? 1u : 0u);
-    ptx::mma_bf16(d_tmem, dh + adv, dx2 + adv, idesc, 1u);
-    ptx::mma_bf16(d_tmem, dl + adv, dx1 + adv, idesc, 1u);
+    const uint64_t adv = (uint64_t)(kk * 32) >> 4;              // x: 16 columns along the row
+    const uint64_t adva = (uint64_t)(kk * 2 * kGroupK) >> 4;     // A: two K groups
+    ptx::mma_bf16(d_tmem, dh + adva, dx1 + adv, idesc, (!first_kt || kk > 0) ? 1u : 0u);
+    ptx::mma_bf16(d_tmem, dh + adva, dx2 + adv, idesc, 1u);
+    ptx::mma_bf16(d_tmem, dl + adva, dx1 + adv, idesc, 1u);
   }
   ptx::mma_commit(empty);
   if (last_kt) ptx::mma_commit(&tfull[acc]);
@@ -393,17 +421,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int n = P.n;
   const uint32_t un = (uint32_t)n;
   const uint32_t nq = (uint32_t)(n + 1);
-  // Lane l generates column 4g + (l % 4) for the pixels du = l / 4 of the
-  // tile's 8-pixel rows dv = 0..15 (tile row 8 dv + du): a warp's load then
-  // covers 8 neighbouring pixels x 4 neighbouring columns, and columns next
-  // to each other in the sorted order often need the same footprint entry
-  // for a pixel, so the request touches fewer sectors.
+  // Lane l generates column 4g + (l % 4) for the pixel du = l / 4 of each of
+  // the tile's 16 rows dv: a warp's load then covers 8 neighbouring pixels x
+  // 4 neighbouring columns, and columns next to each other in the sorted
+  // order often need the same footprint entry for a pixel, so the request
+  // touches fewer sectors.
   const int col = g * kCols + (lane & 3);
   const uint32_t du = (uint32_t)(lane >> 2);
-  // Swizzled shared-memory address of this lane's bf16 in tile row dv * 8 +
-  // du: 16-byte chunk index XOR (row % 8) inside each 1024-byte group of 8
-  // rows (128-byte swizzle); row group dv adds dv * 1024.
-  const uint32_t row_off = du * 128 + ((((uint32_t)col >> 3) ^ du) << 4) + ((uint32_t)col & 7) * 2;
+  // This lane's 16 values of a k-tile are tile rows 16 sigma(du) + dv of
+  // column col: two runs of 8 contiguous bf16 in the M-major layout, in the
+  // swizzle atom of rows 64 (sd / 4) .. +63 of K group col / 8, K row col % 8,
+  // 16-byte chunk (row % 64) / 8 XOR (col % 8).
+  const uint32_t sd = sigma(du), kr = (uint32_t)col & 7u;
+  const uint32_t run_base = ((uint32_t)col >> 3) * kGroupK + (sd >> 2) * kAtomMN + kr * 128;
+  const uint32_t run_off0 = run_base + (((2u * (sd & 3u)) ^ kr) << 4);
+  const uint32_t run_off1 = run_base + (((2u * (sd & 3u) + 1u) ^ kr) << 4);
   uint32_t it = 0, c = 0;
   bool ok = true;
   for (int u = blockIdx.x; u < units; u += gridDim.x) {
@@ -480,7 +512,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           ++x_issued;
         }
         const float w0 = L.w0, w1 = L.w1;
-        uint8_t *st = stage + row_off;
+        const uint32_t st = ptx::smem_u32(stage);
+        uint32_t hw[4], lw[4];
+        float y_even = 0.f;
         auto finish = [&](int t) {
           const int i = t % kDepth;
           float an, af, bn, bf;
@@ -493,10 +527,25 @@ __global__ void __launch_bounds__(kThreads, 1)
           float v0, v1;
           f2_unpack(v, v0, v1);
           const float y = fmaf(w1, v1, w0 * v0);
-          const __nv_bfloat16 hi = __float2bfloat16_rn(y);
-          const __nv_bfloat16 lo = __float2bfloat16_rn(y - __bfloat162float(hi));
-          *reinterpret_cast<__nv_bfloat16 *>(st + t * 1024) = hi;
-          *reinterpret_cast<__nv_bfloat16 *>(st + kTileBytes + t * 1024) = lo;
+          if ((t & 1) == 0) {
+            y_even = y;
+          } else {
+            // Rows t - 1 and t as one word each of hi and lo (row t - 1 in the low half).
+            uint32_t h2, l2;
+            asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h2) : "f"(y), "f"(y_even));
+            const float r_even = y_even - __uint_as_float(h2 << 16);
+            const float r_odd = y - __uint_as_float(h2 & 0xFFFF0000u);
+            asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l2) : "f"(r_odd), "f"(r_even));
+            hw[(t >> 1) & 3] = h2;
+            lw[(t >> 1) & 3] = l2;
+          }
+          if ((t & 7) == 7) {
+            const uint32_t ad = st + ((t >> 3) ? run_off1 : run_off0);
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ad), "r"(hw[0]), "r"(hw[1]), "r"(hw[2]),
+                         "r"(hw[3]));
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ad + kTileBytes), "r"(lw[0]), "r"(lw[1]),
+                         "r"(lw[2]), "r"(lw[3]));
+          }
         };
 #pragma unroll
         for (int t = 0; t < kTileH; ++t) {
@@ -522,11 +571,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (ok && kc > k0 && !drain(c - 1)) ok = false;
     }
     if (ok && !drain(c - 1)) ok = false;
-    if (!ok) break;  // the next unit's first barrier takes every warp out
-    // This lane drains tile row 32 quarter + lane: pixel (l % 8, l / 8 + 4 quarter).
-    // The TMEM loads are warp-collective, so every lane takes part; only
-    // lanes whose pixel lies inside the image store.
-    const int p = p0 + (lane >> 3) + 4 * quarter, q = q0 + (lane & 7);
+    if (!ok) break;
+    // This lane drains tile row 32 quarter + lane = 16 sigma(du) + dv.  The
+    // TMEM loads are warp-collective, so every lane takes part; only lanes
+    // whose pixel lies inside the image store.
+    const int p = p0 + (lane & 15), q = q0 + (int)sigma((uint32_t)(2 * quarter + (lane >> 4)));
     const bool inside = p < n && q < n;
     int pp = p, qp = q;  // P^rot: (p, q) -> (q, n-1-p), applied rot times
     for (int t = 0; t < rot; ++t) {
