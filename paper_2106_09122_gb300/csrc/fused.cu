@@ -119,6 +119,7 @@ struct FusedParams {
   float *part;            // [KS][4][B][rows]
   int *status;
   uint64_t wait_ns;
+  int64_t stall_load;     // test hook: the x load of this k-tile (CTA issue order) is never issued; -1: none
 };
 
 // A lane's column in the current k-tile: the source coordinates a and b of
@@ -413,7 +414,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int Bp = P.Bp;
   const bool producer = threadIdx.x == 0;  // also issues the x tiles' TMA loads
   const uint32_t x_tx = (uint32_t)(8 * Bp) * BK * 2;
-  uint32_t x_issued = 0;                   // x loads issued (producer only)
+  // Producer only: the latest x load issued into stage 0 and stage 1 (k-tile
+  // index + 1; 0: none).
+  static_assert(kStages == 2, "x load bookkeeping");
+  uint32_t x_last0 = 0u, x_last1 = 0u;
 
   const int g = warp;                  // 0..15
   const int quarter = warp & 3;        // TMEM lane quarter this warp may access
@@ -506,10 +510,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         uint8_t *stage = smem + (size_t)s * P.stage_bytes;
-        if (producer) {
+        if (producer && (int64_t)it != P.stall_load) {
           ptx::mbar_arrive_expect_tx(&xfull[s], x_tx);
           ptx::tma_load_2d(stage + 2 * kTileBytes, &map_x, kt * BK, 0, &xfull[s]);
-          ++x_issued;
+          if (s == 0)
+            x_last0 = it + 1;
+          else
+            x_last1 = it + 1;
         }
         const float w0 = L.w0, w1 = L.w1;
         const uint32_t st = ptx::smem_u32(stage);
@@ -601,11 +608,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   // Drain before the memory is released: every lane that issued MMAs commits
   // them to drain_bar (a thread with none arrives at once), and the copies of
-  // x the producer issued land.
+  // x the producer issued land (a stage's earlier copies were consumed by MMAs
+  // before it was refilled, so its latest one is the only one to wait for).
   if (lane == 0) ptx::mma_commit(&drain_bar);
   if (producer) {
-    for (uint32_t i = x_issued > (uint32_t)kStages ? x_issued - (uint32_t)kStages : 0u; i < x_issued; ++i)
-      if (!ptx::mbar_wait_bounded(&xfull[i % kStages], (i / kStages) & 1, lim)) set_abort(&abort_flag, P.status);
+    if (x_last0 && !ptx::mbar_wait_bounded(&xfull[0], ((x_last0 - 1) / kStages) & 1, lim))
+      set_abort(&abort_flag, P.status);
+    if (x_last1 && !ptx::mbar_wait_bounded(&xfull[1], ((x_last1 - 1) / kStages) & 1, lim))
+      set_abort(&abort_flag, P.status);
   }
   if (lane == 0 && !ptx::mbar_wait_bounded(&drain_bar, 0, lim)) set_abort(&abort_flag, P.status);
   __syncthreads();
@@ -700,8 +710,10 @@ size_t psfsim_forward_fused_scratch(const psfsim_plan *h, int B) {
   return f.xs_bytes + f.part_bytes;
 }
 
-cudaError_t psfsim_launch_forward_fused(const psfsim_plan *h, const float *x, int B, float *y, void *scratch,
-                                        cudaStream_t st) {
+// One fused forward per chunk of at most kMaxBp scenes; max_ctas, wait_ns and
+// stall_load serve the test hook (all SMs, 2 s and -1 otherwise).
+static cudaError_t launch_fused(const psfsim_plan *h, const float *x, int B, float *y, void *scratch, int max_ctas,
+                                uint64_t wait_ns, int64_t stall_load, cudaStream_t st) {
   int *status = reinterpret_cast<int *>(h->ws + h->status_off);
   for (int b0 = 0; b0 < B; b0 += kMaxBp) {
     const int Bc = (B - b0) < kMaxBp ? (B - b0) : kMaxBp;
@@ -735,16 +747,27 @@ cudaError_t psfsim_launch_forward_fused(const psfsim_plan *h, const float *x, in
     P.plib = reinterpret_cast<const float *>(h->ws + h->plib_off);
     P.part = part;
     P.status = status;
-    P.wait_ns = 2000000000ull;
+    P.wait_ns = wait_ns;
+    P.stall_load = stall_load;
     if ((e = cudaFuncSetAttribute(fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem)) !=
         cudaSuccess)
       return e;
     const int units = f.m_tiles * f.KS;
-    fused_kernel<<<units < h->num_sms ? units : h->num_sms, kThreads, f.smem, st>>>(mx, P);
+    fused_kernel<<<units < max_ctas ? units : max_ctas, kThreads, f.smem, st>>>(mx, P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = psfsim_launch_reduce_partials(part, 4 * f.KS, Bc, f.rows, h->M, y + (int64_t)b0 * h->M, nullptr, st)) !=
         cudaSuccess)
       return e;
   }
   return cudaSuccess;
+}
+
+cudaError_t psfsim_launch_forward_fused(const psfsim_plan *h, const float *x, int B, float *y, void *scratch,
+                                        cudaStream_t st) {
+  return launch_fused(h, x, B, y, scratch, h->num_sms, 2000000000ull, -1, st);
+}
+
+cudaError_t psfsim_launch_forward_fused_stall(const psfsim_plan *h, const float *x, int B, float *y, void *scratch,
+                                              uint64_t wait_ns, int64_t stall_load, cudaStream_t st) {
+  return launch_fused(h, x, B, y, scratch, 1, wait_ns, stall_load, st);
 }

@@ -107,6 +107,10 @@ cudaError_t psfsim_launch_adjoint_sym(const psfsim_plan *h, const float *g, int 
 size_t psfsim_forward_fused_scratch(const psfsim_plan *h, int B);
 cudaError_t psfsim_launch_forward_fused(const psfsim_plan *h, const float *x, int B, float *y, void *scratch,
                                         cudaStream_t st);
+// Test hook: the fused forward of <= 32 scenes on one CTA with every wait
+// bounded by wait_ns and the x load of k-tile number stall_load never issued.
+cudaError_t psfsim_launch_forward_fused_stall(const psfsim_plan *h, const float *x, int B, float *y, void *scratch,
+                                              uint64_t wait_ns, int64_t stall_load, cudaStream_t st);
 cudaError_t psfsim_launch_adjoint_split(const psfsim_plan *h, const float *g, int B, float *gx, void *scratch,
                                         cudaStream_t st);
 
