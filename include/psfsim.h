@@ -104,9 +104,11 @@ int psfsim_workspace_bytes(int n, int n_r, int64_t K, int storage, size_t *bytes
  * all N^2 scene pixels; Eq. 4-5).
  *   d_lib       device float32 [n_r][n][n], 16-byte aligned; read during the
  *               build only (FUSED storage keeps its own copy in the
- *               workspace, each pixel's 2 x 2 bilinear footprint as a float4).  FUSED needs an even N (it uses the exact
- *               quarter-turn symmetry of the scene grid) and synchronizes the
- *               stream once.
+ *               workspace: for every radial bracket and pixel, the 2 x 2
+ *               bilinear footprints of both PSFs of the bracket in one
+ *               32-byte entry, and a table of its columns).  FUSED needs an
+ *               even N (it uses the exact quarter-turn symmetry of the scene
+ *               grid) and synchronizes the stream once.
  *   h_radii     host double [n_r], strictly increasing offsets in lambda/D.
  *   s           PSF pixel scale (lambda/D per pixel).  A depends on s only
  *               through the radii; it is validated (> 0).

@@ -375,6 +375,9 @@ __device__ __forceinline__ void issue_stage_mmas(const FusedParams &P, uint8_t *
   if (last_kt) ptx::mma_commit(&tfull[acc]);
 }
 
+// kStallHook: the test hook's instantiation, the only one that reads
+// P.stall_load.
+template <bool kStallHook>
 __global__ void __launch_bounds__(kThreads, 1)
     fused_kernel(const __grid_constant__ CUtensorMap map_x, const FusedParams P) {
   extern __shared__ uint8_t smem_raw[];
@@ -382,6 +385,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ __align__(8) uint64_t xfull[kStages], gfull[kStages], empty[kStages], tfull[2], tempty[2];
   __shared__ __align__(8) uint64_t drain_bar;
   __shared__ int arrivals[kStages];
+  __shared__ uint32_t x_last[kStages];  // test hook only: latest x load issued into each stage (k-tile + 1)
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -392,6 +396,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       ptx::mbar_init(&gfull[s], kWarps);
       ptx::mbar_init(&empty[s], 1);
       arrivals[s] = 0;
+      x_last[s] = 0u;
     }
     for (int a = 0; a < 2; ++a) {
       ptx::mbar_init(&tfull[a], 1);
@@ -414,10 +419,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int Bp = P.Bp;
   const bool producer = threadIdx.x == 0;  // also issues the x tiles' TMA loads
   const uint32_t x_tx = (uint32_t)(8 * Bp) * BK * 2;
-  // Producer only: the latest x load issued into stage 0 and stage 1 (k-tile
-  // index + 1; 0: none).
-  static_assert(kStages == 2, "x load bookkeeping");
-  uint32_t x_last0 = 0u, x_last1 = 0u;
+  uint32_t x_issued = 0;  // x loads issued (producer only)
 
   const int g = warp;                  // 0..15
   const int quarter = warp & 3;        // TMEM lane quarter this warp may access
@@ -510,13 +512,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         uint8_t *stage = smem + (size_t)s * P.stage_bytes;
-        if (producer && (int64_t)it != P.stall_load) {
+        if (producer && (!kStallHook || (int64_t)it != P.stall_load)) {
           ptx::mbar_arrive_expect_tx(&xfull[s], x_tx);
           ptx::tma_load_2d(stage + 2 * kTileBytes, &map_x, kt * BK, 0, &xfull[s]);
-          if (s == 0)
-            x_last0 = it + 1;
-          else
-            x_last1 = it + 1;
+          ++x_issued;
+          if (kStallHook) x_last[s] = it + 1;
         }
         const float w0 = L.w0, w1 = L.w1;
         const uint32_t st = ptx::smem_u32(stage);
@@ -608,14 +608,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   // Drain before the memory is released: every lane that issued MMAs commits
   // them to drain_bar (a thread with none arrives at once), and the copies of
-  // x the producer issued land (a stage's earlier copies were consumed by MMAs
-  // before it was refilled, so its latest one is the only one to wait for).
+  // x the producer issued land.  Without the test hook the copies alternate
+  // between the stages in issue order, so the last kStages issued are the
+  // ones to wait for; with it one copy may be missing, and the latest copy
+  // issued into each stage is waited for (a stage's earlier copies were
+  // consumed by MMAs before it was refilled).
   if (lane == 0) ptx::mma_commit(&drain_bar);
   if (producer) {
-    if (x_last0 && !ptx::mbar_wait_bounded(&xfull[0], ((x_last0 - 1) / kStages) & 1, lim))
-      set_abort(&abort_flag, P.status);
-    if (x_last1 && !ptx::mbar_wait_bounded(&xfull[1], ((x_last1 - 1) / kStages) & 1, lim))
-      set_abort(&abort_flag, P.status);
+    if (kStallHook) {
+      for (int st2 = 0; st2 < kStages; ++st2)
+        if (x_last[st2] && !ptx::mbar_wait_bounded(&xfull[st2], ((x_last[st2] - 1) / kStages) & 1, lim))
+          set_abort(&abort_flag, P.status);
+    } else {
+      for (uint32_t i = x_issued > (uint32_t)kStages ? x_issued - (uint32_t)kStages : 0u; i < x_issued; ++i)
+        if (!ptx::mbar_wait_bounded(&xfull[i % kStages], (i / kStages) & 1, lim)) set_abort(&abort_flag, P.status);
+    }
   }
   if (lane == 0 && !ptx::mbar_wait_bounded(&drain_bar, 0, lim)) set_abort(&abort_flag, P.status);
   __syncthreads();
@@ -749,11 +756,12 @@ static cudaError_t launch_fused(const psfsim_plan *h, const float *x, int B, flo
     P.status = status;
     P.wait_ns = wait_ns;
     P.stall_load = stall_load;
-    if ((e = cudaFuncSetAttribute(fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem)) !=
+    auto kernel = stall_load >= 0 ? fused_kernel<true> : fused_kernel<false>;
+    if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem)) !=
         cudaSuccess)
       return e;
     const int units = f.m_tiles * f.KS;
-    fused_kernel<<<units < max_ctas ? units : max_ctas, kThreads, f.smem, st>>>(mx, P);
+    kernel<<<units < max_ctas ? units : max_ctas, kThreads, f.smem, st>>>(mx, P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = psfsim_launch_reduce_partials(part, 4 * f.KS, Bc, f.rows, h->M, y + (int64_t)b0 * h->M, nullptr, st)) !=
         cudaSuccess)
