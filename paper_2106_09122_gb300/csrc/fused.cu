@@ -56,7 +56,9 @@
 // are handed over through mbarriers only.  A lane keeps four rows' footprint
 // loads in flight, and the stream runs on across the k-tiles of an
 // accumulation chunk: while a k-tile's last rows are finished, the next
-// k-tile's first rows are already loading.  Warps also drain the TMEM
+// k-tile's first rows are already loading.  A k-tile in which every lane's
+// 16 rows lie beyond one edge of the library (the image corners at many
+// angles) is written as zeros without loads.  Warps also drain the TMEM
 // accumulator of rotation g / 4 for rows 32 (g % 4) .. +31 every kChunk
 // k-tiles into a running FP32 sum kept in a third TMEM region (the tensor
 // core's FP32 accumulation is not round-to-nearest, so long accumulations
@@ -306,6 +308,18 @@ __device__ __forceinline__ void lane_start(const FusedCol &c, int p0, int q0, ui
   L.w1 = c.w1;
 }
 
+// True when all 16 rows of a lane's column, from its current start L, fall
+// beyond one edge of the library (their footprints are all zero): a and b
+// only grow along the rows (C2, S2 >= 0 in the quadrant), so the first and
+// the last row decide.
+__device__ __forceinline__ bool rows_outside(const LaneCol &L, uint32_t un) {
+  const long long a0 = (long long)L.a, b0 = (long long)L.b;
+  const long long a15 = a0 + (long long)(kTileH - 1) * (long long)L.S2;
+  const long long b15 = b0 + (long long)(kTileH - 1) * (long long)L.C2;
+  const long long lim = (long long)(un + 1u) << kFixShift;  // padded index > n
+  return a15 < 0 || a0 >= lim || b15 < 0 || b0 >= lim;
+}
+
 // The two bilinear weights of one axis, in units of 2^-32, from the 32-bit
 // fraction f of a source coordinate: (2^32 - f, f), each from its exact
 // integer, so each is accurate relative to itself however small: f converts
@@ -486,6 +500,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       // are finished, the first rows of the next are already being loaded.
       LaneCol L;
       lane_start(P.cols[(int64_t)kc * BK + col], p0, q0, du, L);
+      // A k-tile whose footprints are all zero for the whole warp is written
+      // as zeros without loading anything.
+      bool skip = __all_sync(0xffffffffu, rows_outside(L, un));
       Entry ent[kDepth];
       uint32_t fa[kDepth], fb[kDepth];
       auto issue = [&](int t) {
@@ -498,8 +515,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         L.a += L.S2;
         L.b += L.C2;
       };
+      if (!skip) {
 #pragma unroll
-      for (int t = 0; t < kDepth; ++t) issue(t);
+        for (int t = 0; t < kDepth; ++t) issue(t);
+      }
       for (int kt = kc; kt < kc1; ++kt, ++it) {
         const bool more = kt + 1 < kc1;
         // The next column's entry, read where its first row is issued.
@@ -518,6 +537,25 @@ __global__ void __launch_bounds__(kThreads, 1)
           ++x_issued;
           if (kStallHook) x_last[s] = it + 1;
         }
+        const uint32_t st = ptx::smem_u32(stage);
+        if (skip) {
+          const uint32_t z = 0u;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint32_t ad = st + (h ? run_off1 : run_off0);
+            asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(ad), "r"(z));
+            asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};" ::"r"(ad + kTileBytes), "r"(z));
+          }
+          if (more) {
+            cn = *next_col;
+            lane_start(cn, p0, q0, du, L);
+            skip = __all_sync(0xffffffffu, rows_outside(L, un));
+            if (!skip) {
+#pragma unroll
+              for (int t = 0; t < kDepth; ++t) issue(kTileH + t);
+            }
+          }
+        } else {
         const float w0 = L.w0, w1 = L.w1;
         const uint32_t st = ptx::smem_u32(stage);
         uint32_t hw[4], lw[4];
@@ -557,10 +595,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int t = 0; t < kTileH; ++t) {
           // Rows t + kDepth >= kTileH belong to the next k-tile's column.
-          if (t == kTileH - kDepth && more) cn = *next_col;
-          if (t == kTileH - kDepth && more) lane_start(cn, p0, q0, du, L);
+          if (t == kTileH - kDepth && more) {
+            cn = *next_col;
+            lane_start(cn, p0, q0, du, L);
+            skip = __all_sync(0xffffffffu, rows_outside(L, un));
+          }
           finish(t);
-          if (t + kDepth < kTileH || more) issue(t + kDepth);
+          if (t + kDepth < kTileH || (more && !skip)) issue(t + kDepth);
+        }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
