@@ -201,8 +201,9 @@ def _fused_config(w, world):
 
 def _fused_mma_flops(plan, scenes):
     """bf16 MMA flops one fused launch issues: per 128-row m-tile and 64-column k-tile of
-    the quadrant's columns, three products (hi x1, hi x2, lo x1) of N = 4 Bp."""
-    Bp = 16 if scenes <= 16 else 32
+    the quadrant's columns, three products (hi x1, hi x2, lo x1) of N = 4 Bp (Bp = 16, 32 or
+    64 scenes per launch)."""
+    Bp = 16 if scenes <= 16 else (32 if scenes <= 32 else 64)
     rows = (plan.M + 127) // 128 * 128
     ldx = (plan.info.K_stored + 63) // 64 * 64
     return 2.0 * rows * ldx * 4 * Bp * 3
@@ -389,6 +390,37 @@ def _fused_crop_comparator(dev, stream, w, lib32, fused_plan, X_np, with_oracle)
                                   "rows_checked": len(rows), "scenes_checked": 4}
     del fp, A, Xcrop, Ymm, Xf, Yf, scr
     torch.cuda.empty_cache()
+    return out
+
+
+def _fused_64_scenes(dev, stream, w, lib32, plan, peaks, with_oracle):
+    """The fused 512^2 workload with 64 scenes per launch (the kernel's 64-scene form: MMA
+    N = 256, one accumulator), beside the 32-scene headline: the same generation carries twice
+    the tensor work."""
+    import torch
+    from synth import workloads
+    B = 64
+    X_np = workloads.scene_batch(w, B, kind="two_ring").astype(np.float32)
+    X = torch.from_numpy(X_np).to(dev)
+    Y = torch.empty((B, w.M), device=dev)
+    scr = torch.empty(plan.forward_scratch_bytes(B), dtype=torch.uint8, device=dev)
+    ms = _timed(lambda: plan.forward(X, out=Y, scratch=scr), 5, stream)
+    flops = _fused_mma_flops(plan, B)
+    out = {"workload": "fused_512 with 64 two-ring scenes per psfsim_forward call (one launch)",
+           "images_per_s": B / (ms / 1e3), "ms_per_call": ms,
+           "roofline": {"bound": "tensor", "achieved": flops / (ms / 1e3) / 1e12, "peak": peaks["bf16_sustained"],
+                        "unit": "TFLOP/s", "frac": flops / (ms / 1e3) / 1e12 / peaks["bf16_sustained"],
+                        "flops_per_launch": flops},
+           "status": plan.sync_status()}
+    if with_oracle:
+        from oracle import psfsim_oracle as O
+        rows = np.sort(np.random.default_rng(64).choice(w.M, 8, replace=False))
+        ref, bound, _ = _oracle_rows_fused(w, lib32, X_np, rows)
+        Yr = Y[:, torch.from_numpy(rows).to(dev)].double().cpu().numpy()
+        rel = O.bound_relative_error(Yr, ref, bound, floor=O.FLT_MIN)
+        out["error_vs_oracle"] = {"max_bound_rel_error": float(rel.max()), "rows_checked": len(rows),
+                                  "scenes_checked": B}
+    del X, Y, scr
     return out
 
 
@@ -1114,10 +1146,12 @@ def main():
         dev = torch.device("cuda", local_rank)
         stream = torch.cuda.current_stream()
         out["fp32_gemm_comparator"] = _fused_crop_comparator(dev, stream, w, lib32, plan, X_np, with_oracle)
+        fused64 = _fused_64_scenes(dev, stream, w, lib32, plan, _peaks(), with_oracle)
         del plan, Y, X
         torch.cuda.empty_cache()
         hbm = _peaks()["hbm"]
         out["other_workloads"] = {
+            "fused_512_64_scenes": fused64,
             "adjoint_fit_128": _entry_fit128(dev, stream, with_oracle),
             "batched_split_bf16_256_8_wavelengths": _path_batched(dev, stream, hbm, with_oracle),
             "batched_bf16_256_8_wavelengths": _path_bf16(dev, stream, hbm, with_oracle),

@@ -17,7 +17,7 @@ extern "C" {
 #endif
 
 /* The tensor-core forward of psfsim_forward (SPLIT_BF16 or BF16 plan, B <= 80
- * scenes; or FUSED plan, B <= 32 scenes; same scratch as psfsim_forward) run
+ * scenes; or FUSED plan, B <= 64 scenes; same scratch as psfsim_forward) run
  * on ONE CTA with every device-side wait bounded by wait_ns nanoseconds
  * (1 us .. 2 s), and with the shared-memory load number stall_load (counted
  * from 0 in the CTA's issue order: for FUSED, the x tile of the CTA's k-tile

@@ -325,7 +325,7 @@ int psfsim_debug_forward_stall(psfsim_t h, const float *d_x, int B, float *d_y, 
   if (!h || !d_x || !d_y || B < 1 || B > 80) return PSFSIM_ERR_ARG;
   if (wait_ns < 1000 || wait_ns > 2000000000ull || stall_load < -1) return PSFSIM_ERR_ARG;
   if (h->storage == PSFSIM_FUSED) {
-    if (B > 32) return PSFSIM_ERR_ARG;
+    if (B > 64) return PSFSIM_ERR_ARG;
     if (!d_scratch || !aligned(d_scratch, 256) || scratch_bytes < psfsim_forward_fused_scratch(h, B))
       return PSFSIM_ERR_WORKSPACE;
     return psfsim_launch_forward_fused_stall(h, d_x, B, d_y, d_scratch, wait_ns, stall_load,

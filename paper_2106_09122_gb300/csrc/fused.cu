@@ -63,7 +63,9 @@
 // k-tiles into a running FP32 sum kept in a third TMEM region (the tensor
 // core's FP32 accumulation is not round-to-nearest, so long accumulations
 // drift; the sums are added on the CUDA cores, and keeping them in TMEM leaves
-// the registers to generation).  Every wait is bounded; after a timeout every
+// the registers to generation).  A launch carries 16, 32 or 64 scenes; with 64
+// (N = 256) TMEM holds a single accumulator beside the sums, and a chunk's
+// drain comes right after the next chunk's first k-tile is generated.  Every wait is bounded; after a timeout every
 // later wait fails at once, each warp leaves its loop, and each role waits
 // (bounded) for the asynchronous work it issued before the CTA releases its
 // memory.
@@ -81,10 +83,11 @@ constexpr int kWarps = 16;                   // every warp generates; see the fi
 constexpr int kThreads = kWarps * 32;
 constexpr int kStages = 2;
 constexpr int kChunk = 5;                    // k-tiles per accumulation: 5 x 4 x 3 = 60 MMAs
-constexpr int kMaxBp = 32;
+constexpr int kMaxBp = 64;                   // scenes per launch: 16, 32 or 64 (padded)
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kAccStride = 128;         // two accumulators of 4Bp <= 128 columns
+constexpr uint32_t kAccStride = 128;         // Bp <= 32: two accumulators of 4Bp <= 128 columns
 constexpr uint32_t kSumCol = 256;            // running sums: columns 256 .. 256 + 4Bp
+// Bp = 64 ("wide"): one accumulator of 256 columns, the sums beside it.
 constexpr uint32_t kTileBytes = BM * BK * 2;
 constexpr int kTileW = 8, kTileH = 16;       // M-tile: 8 x 16 image pixels
 constexpr int kCols = BK / kWarps;           // columns per generator warp per k-tile
@@ -358,14 +361,18 @@ __host__ __device__ constexpr uint32_t sigma(uint32_t du) { return (du & 4u) | (
 // x tile, and (first k-tile of a chunk) for the accumulator to be drained;
 // then 4 k-steps of three N = 4Bp MMAs, a commit that frees the stage, and
 // (last k-tile of the chunk) one that hands the accumulator to the drain.
+template <bool kWide>
 __device__ __forceinline__ void issue_stage_mmas(const FusedParams &P, uint8_t *stage, uint64_t *xfull,
                                                  uint64_t *gfull, uint64_t *empty, uint64_t *tfull, uint64_t *tempty,
                                                  uint32_t par, uint32_t c, bool first_kt, bool last_kt, uint32_t tbase,
                                                  volatile int *abort_flag) {
   const uint64_t lim = P.wait_ns;
-  const uint32_t acc = c & 1;
+  // Bp <= 32: accumulator c % 2, each used every other chunk; Bp = 64: the one
+  // accumulator, drained after every chunk.
+  const uint32_t acc = kWide ? 0u : (c & 1);
+  const uint32_t drained = kWide ? ((c & 1) ^ 1) : (((c >> 1) & 1) ^ 1);
   if (!ptx::mbar_wait_bounded(gfull, par, lim) || !ptx::mbar_wait_bounded(xfull, par, lim) ||
-      (first_kt && !ptx::mbar_wait_bounded(&tempty[acc], ((c >> 1) & 1) ^ 1, lim))) {
+      (first_kt && !ptx::mbar_wait_bounded(&tempty[acc], drained, lim))) {
     set_abort(abort_flag, P.status);
     return;
   }
@@ -391,7 +398,9 @@ __device__ __forceinline__ void issue_stage_mmas(const FusedParams &P, uint8_t *
 
 // kStallHook: the test hook's instantiation, the only one that reads
 // P.stall_load.
-template <bool kStallHook>
+// kWide: the Bp = 64 form (one accumulator, the chunk's drain moved to the
+// next chunk's first k-tile).
+template <bool kWide, bool kStallHook>
 __global__ void __launch_bounds__(kThreads, 1)
     fused_kernel(const __grid_constant__ CUtensorMap map_x, const FusedParams P) {
   extern __shared__ uint8_t smem_raw[];
@@ -466,12 +475,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tsum = tbase + ((uint32_t)(quarter * 32) << 16) + kSumCol + rot * Bp;
     bool first = true;  // the unit's first drain writes the sums instead of adding
     auto drain = [&](uint32_t cc) -> bool {
-      const uint32_t acc = cc & 1;
-      if (!warp_wait(&tfull[acc], (cc >> 1) & 1, &abort_flag, P.status, lim)) return false;
+      const uint32_t acc = kWide ? 0u : (cc & 1);
+      if (!warp_wait(&tfull[acc], kWide ? (cc & 1) : ((cc >> 1) & 1), &abort_flag, P.status, lim)) return false;
       ptx::tc_fence_after();
       const uint32_t tacc = tbase + ((uint32_t)(quarter * 32) << 16) + acc * kAccStride + rot * Bp;
 #pragma unroll
-      for (int qq = 0; qq < kMaxBp / 16; ++qq) {
+      for (int qq = 0; qq < (kWide ? 64 : 32) / 16; ++qq) {
         if (qq * 16 < Bp) {
           float v[16], sm[16];
           ptx::tmem_ld16(tacc + qq * 16, v);
@@ -534,6 +543,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (producer && (!kStallHook || (int64_t)it != P.stall_load)) {
           ptx::mbar_arrive_expect_tx(&xfull[s], x_tx);
           ptx::tma_load_2d(stage + 2 * kTileBytes, &map_x, kt * BK, 0, &xfull[s]);
+          if (kWide)  // 8 Bp = 512 rows: two boxes of 256
+            ptx::tma_load_2d(stage + 2 * kTileBytes + 256 * 128, &map_x, kt * BK, 256, &xfull[s]);
           ++x_issued;
           if (kStallHook) x_last[s] = it + 1;
         }
@@ -604,6 +615,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (t + kDepth < kTileH || (more && !skip)) issue(t + kDepth);
         }
         }
+        // Bp = 64: the previous chunk's accumulator is drained here, after this
+        // chunk's first k-tile is generated and before this warp arrives for
+        // it (the first k-tile's MMAs wait for the drain; the generators do not).
+        if (kWide && kt == kc && kc > k0 && !drain(c - 1)) {
+          ok = false;
+          break;
+        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (lane == 0) {
@@ -611,13 +629,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           // The warp that completes the stage issues its MMAs (the counter
           // only grows: every use of a stage adds kWarps).
           if ((atomicAdd(&arrivals[s], 1) & (kWarps - 1)) == kWarps - 1) {
-            issue_stage_mmas(P, stage, &xfull[s], &gfull[s], &empty[s], tfull, tempty, par, c, kt == kc,
-                             kt == kc1 - 1, tbase, &abort_flag);
+            issue_stage_mmas<kWide>(P, stage, &xfull[s], &gfull[s], &empty[s], tfull, tempty, par, c, kt == kc,
+                                    kt == kc1 - 1, tbase, &abort_flag);
           }
         }
         __syncwarp();
       }
-      if (ok && kc > k0 && !drain(c - 1)) ok = false;
+      if (!kWide && ok && kc > k0 && !drain(c - 1)) ok = false;
     }
     if (ok && !drain(c - 1)) ok = false;
     if (!ok) break;
@@ -634,7 +652,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     float *out = P.part + ((int64_t)(ks * 4 + rot) * P.B) * P.rows + (int64_t)pp * n + qp;
 #pragma unroll
-    for (int qq = 0; qq < kMaxBp / 16; ++qq) {
+    for (int qq = 0; qq < (kWide ? 64 : 32) / 16; ++qq) {
       if (qq * 16 < Bp) {
         float v[16];
         ptx::tmem_ld16(tsum + qq * 16, v);
@@ -704,7 +722,7 @@ struct FusedPlanInfo {
 
 FusedPlanInfo fused_info(const psfsim_plan *h, int Bc) {
   FusedPlanInfo f;
-  f.Bp = Bc <= 16 ? 16 : 32;
+  f.Bp = Bc <= 16 ? 16 : (Bc <= 32 ? 32 : 64);
   f.rows = psfsim_round_up(h->M, BM);
   f.tiles_q = (h->n + kTileW - 1) / kTileW;
   f.m_tiles = f.tiles_q * ((h->n + kTileH - 1) / kTileH);
@@ -775,7 +793,8 @@ static cudaError_t launch_fused(const psfsim_plan *h, const float *x, int B, flo
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     CUtensorMap mx;
-    if (!encode_x_map(&mx, xs, (uint64_t)f.ldx, (uint64_t)(8 * f.Bp), (uint32_t)(8 * f.Bp)))
+    // a TMA box holds at most 256 rows; Bp = 64 loads its 512 rows as two boxes
+    if (!encode_x_map(&mx, xs, (uint64_t)f.ldx, (uint64_t)(8 * f.Bp), (uint32_t)(8 * f.Bp < 256 ? 8 * f.Bp : 256)))
       return cudaErrorInvalidValue;
     FusedParams P;
     P.n = h->n;
@@ -798,7 +817,9 @@ static cudaError_t launch_fused(const psfsim_plan *h, const float *x, int B, flo
     P.status = status;
     P.wait_ns = wait_ns;
     P.stall_load = stall_load;
-    auto kernel = stall_load >= 0 ? fused_kernel<true> : fused_kernel<false>;
+    const bool wide = f.Bp == 64;
+    auto kernel = wide ? (stall_load >= 0 ? fused_kernel<true, true> : fused_kernel<true, false>)
+                       : (stall_load >= 0 ? fused_kernel<false, true> : fused_kernel<false, false>);
     if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem)) !=
         cudaSuccess)
       return e;

@@ -97,7 +97,7 @@ def test_stall_hook_rejects_bad_limits():
     plan.free()
 
 
-def _tiny_fused_plan():
+def _tiny_fused_plan(scenes=3):
     from paper_2106_09122_gb300 import Plan
     rng = np.random.default_rng(404)
     n, N, S = 40, 32, 0.3
@@ -105,7 +105,7 @@ def _tiny_fused_plan():
     lib32 = rng.uniform(0.0, 1.0, (12, n, n)).astype(np.float32)
     plan = Plan(torch.from_numpy(lib32).to(DEV), radii, 0.5, N=N, S=S, storage="fused")
     A = O.build_A(lib32.astype(np.float64), radii, N, S)
-    x = rng.uniform(0.0, 1.0, (3, N * N)).astype(np.float32)
+    x = rng.uniform(0.0, 1.0, (scenes, N * N)).astype(np.float32)
     return plan, A, x
 
 
@@ -116,13 +116,14 @@ def _check_fused(y, A, x):
     assert rel.max() <= 2.5e-5, rel.max()
 
 
-@pytest.mark.parametrize("stall_load", [0, 1, 3])
-def test_fused_wait_that_runs_out_reports_timeout_and_leaves_the_plan_usable(stall_load):
+@pytest.mark.parametrize("stall_load,scenes", [(0, 3), (1, 3), (3, 3), (1, 40)])
+def test_fused_wait_that_runs_out_reports_timeout_and_leaves_the_plan_usable(stall_load, scenes):
+    # 40 scenes run the 64-scene form (one accumulator, two boxes per scene tile)
     from paper_2106_09122_gb300 import _binding as B
-    plan, A, x_np = _tiny_fused_plan()
+    plan, A, x_np = _tiny_fused_plan(scenes)
     x = torch.from_numpy(x_np).to(DEV)
-    y = torch.zeros((3, plan.M), device=DEV)
-    scr = torch.empty(plan.forward_scratch_bytes(3), dtype=torch.uint8, device=DEV)
+    y = torch.zeros((scenes, plan.M), device=DEV)
+    scr = torch.empty(plan.forward_scratch_bytes(scenes), dtype=torch.uint8, device=DEV)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     assert _stall(plan, x, y, scr, 1_000_000, stall_load) == B.OK
@@ -152,8 +153,8 @@ def test_fused_stall_hook_without_a_stall_is_a_correct_one_cta_forward():
 def test_fused_stall_hook_rejects_batches_beyond_one_launch():
     from paper_2106_09122_gb300 import _binding as B
     plan, _, _ = _tiny_fused_plan()
-    x = torch.zeros((33, plan.K), device=DEV)
-    y = torch.zeros((33, plan.M), device=DEV)
-    scr = torch.empty(plan.forward_scratch_bytes(33), dtype=torch.uint8, device=DEV)
+    x = torch.zeros((65, plan.K), device=DEV)
+    y = torch.zeros((65, plan.M), device=DEV)
+    scr = torch.empty(plan.forward_scratch_bytes(65), dtype=torch.uint8, device=DEV)
     assert _stall(plan, x, y, scr, 1_000_000, 0) == B.ERR_ARG
     plan.free()

@@ -59,10 +59,12 @@ def test_ipac_shape_forward_and_adjoint(interp):
     assert plan.sync_status() == 0
 
 
-def test_fused_512_full_batch_as_benchmarked():
+@pytest.mark.parametrize("scenes", [None, 64])
+def test_fused_512_full_batch_as_benchmarked(scenes):
+    # None: the benchmarked batch (32 scenes); 64: the 64-scene form of the kernel
     w = workloads.fused_512()
     lib32 = w.library().astype(np.float32)
-    B = w.extra["scenes"]
+    B = scenes or w.extra["scenes"]
     X = workloads.scene_batch(w, B, kind="two_ring").astype(np.float32)
     plan = _plan(lib32, w.radii, w.s, N=w.N, S=w.S, storage="fused")
     Xd = torch.from_numpy(X).to(DEV)
