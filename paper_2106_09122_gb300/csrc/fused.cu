@@ -114,11 +114,10 @@ struct __align__(16) FusedCol {
 static_assert(sizeof(FusedCol) == 48, "FusedCol layout");
 
 struct FusedParams {
-  int n, N, Bp, B, KS, m_tiles, k_tiles, tiles_q;
-  int64_t M, rows, K0v;
+  int n, Bp, B, KS, m_tiles, k_tiles, tiles_q;
+  int64_t rows;
   uint32_t stage_bytes;
-  uint32_t pair_entries;  // entries per bracket pair, (n + 1)^2
-  uint32_t zero_entry;    // index of the all-zero entry after the last pair
+  uint32_t zero_entry;    // index of the all-zero entry after the last bracket pair's (n + 1)^2 entries
   const FusedCol *cols;   // the angle-sorted columns, padded to whole k-tiles
   const float *plib;      // pair entries, 8 floats each
   float *part;            // [KS][4][B][rows]
@@ -798,19 +797,15 @@ static cudaError_t launch_fused(const psfsim_plan *h, const float *x, int B, flo
       return cudaErrorInvalidValue;
     FusedParams P;
     P.n = h->n;
-    P.N = h->N;
     P.Bp = f.Bp;
     P.B = Bc;
     P.KS = f.KS;
     P.m_tiles = f.m_tiles;
     P.tiles_q = f.tiles_q;
     P.k_tiles = f.k_tiles;
-    P.M = h->M;
     P.rows = f.rows;
-    P.K0v = h->K_valid;
     P.stage_bytes = f.stage_bytes;
-    P.pair_entries = (uint32_t)((h->n + 1) * (h->n + 1));
-    P.zero_entry = (uint32_t)(h->n_r - 1) * P.pair_entries;
+    P.zero_entry = (uint32_t)(h->n_r - 1) * (uint32_t)((h->n + 1) * (h->n + 1));
     P.cols = reinterpret_cast<const FusedCol *>(h->ws + h->cols_off);
     P.plib = reinterpret_cast<const float *>(h->ws + h->plib_off);
     P.part = part;
