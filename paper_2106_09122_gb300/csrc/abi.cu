@@ -72,6 +72,7 @@ int common_build(const float *d_lib, const double *h_radii, int n_r, int n, doub
   h->libmax_off = L.libmax_off;
   h->plib_off = L.plib_off;
   h->cols_off = L.cols_off;
+  h->mtorder_off = L.mtorder_off;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = PSFSIM_OK;
   if (cudaGetDevice(&h->device) != cudaSuccess ||

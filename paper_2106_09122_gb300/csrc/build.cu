@@ -362,6 +362,7 @@ WsLayout psfsim_layout(int n, int64_t K, int storage, int n_r) {
   L.plib_off = storage == PSFSIM_FUSED ? take(psfsim_pair_library_bytes(n, n_r)) : -1;
   // ... and the generators' column table.
   L.cols_off = storage == PSFSIM_FUSED ? take(psfsim_fused_columns_bytes(K)) : -1;
+  L.mtorder_off = storage == PSFSIM_FUSED ? take(psfsim_fused_mtile_order_bytes(n)) : -1;
   L.total = off;
   (void)n_r;
   return L;

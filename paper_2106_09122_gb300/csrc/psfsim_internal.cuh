@@ -39,7 +39,7 @@ struct psfsim_plan {
   char *ws;
   size_t ws_bytes;
   int64_t a_off, lo_off, scale_off, geom_off, order_off, bstart_off, pts_off, status_off, libmax_off, plib_off,
-      cols_off;
+      cols_off, mtorder_off;
   int device, num_sms;
   int fit_ks;           // column splits of the fit-gradient forward, fixed at first use (0: not yet)
   CUtensorMap lib_map;  // 3D tensor map over the library for TMA staging
@@ -48,7 +48,7 @@ struct psfsim_plan {
 // Workspace layout for a given shape; returns total bytes.
 struct WsLayout {
   int64_t ld, a_off, lo_off, scale_off, geom_off, order_off, bstart_off, pts_off, status_off, libmax_off, plib_off,
-      cols_off, total;
+      cols_off, mtorder_off, total;
 };
 WsLayout psfsim_layout(int n, int64_t K, int storage, int n_r);
 // FUSED storage's copy of the library: one 32-byte pair entry per bracket
@@ -58,6 +58,8 @@ int64_t psfsim_pair_library_bytes(int n, int n_r);
 // ... and its column table: the generators' (angle-sorted) columns, with
 // their starting coordinates, steps and weights, padded to whole k-tiles.
 int64_t psfsim_fused_columns_bytes(int64_t K);
+// ... and its M-tile order (the image's 8 x 16 pixel tiles, nearest the centre first).
+int64_t psfsim_fused_mtile_order_bytes(int n);
 cudaError_t psfsim_launch_pair_library(psfsim_plan *h, cudaStream_t st);
 
 // Kernel launchers (return cudaError_t of the launch).
