@@ -41,7 +41,8 @@ constexpr uint32_t kTmemColsNarrow = 256, kAccStrideNarrow = 128;
 constexpr uint32_t kTileBytes = BM * BK * 2;
 constexpr int kMaxBp = 80;       // 3 * Bp <= 256 (MMA N and TMA box limits), Bp % 16 == 0
 constexpr int kMaxJobs = 16;
-constexpr int kDefaultChunk = 4; // k-tiles (of 64) per TMEM accumulation
+constexpr int kDefaultChunk = 4; // k-tiles (of 64) per TMEM accumulation, split-BF16 storage
+constexpr int kDefaultChunkHiMulti = 2;  // BF16 storage (hi alone), several jobs in one launch
 constexpr int kMaxMmas = 64;     // accumulating MMAs between drains (bounds the FP32 drift)
 
 // One product S_j = A_j Z_j of a (possibly multi-job) launch.
@@ -372,7 +373,9 @@ struct MultiPlan {
 };
 
 // Tile/launch shape of a multi-job product.  `tune` fields of 0 take defaults:
-// chunk = kDefaultChunk k-tiles per TMEM accumulation; split factors chosen so
+// chunk = kDefaultChunk k-tiles per TMEM accumulation; without lo, the most
+// that fit for one job and kDefaultChunkHiMulti for several (the fastest
+// measured on one 128^2 job and on eight 256^2 jobs); split factors chosen so
 // that the whole launch has about units_per_sm work units per SM (or, for a
 // single job without tuning, the smallest split that fills the SMs evenly);
 // as many smem stages as fit.
@@ -441,7 +444,7 @@ MultiPlan plan_multi(const JobSpec *jobs, int nj, const psfsim_tuning_t *tune) {
   // accumulate between drains.
   const int max_chunk = kMaxMmas / ((any_lo ? 2 : 1) * (BK / 16));
   mp.chunk = tune && tune->chunk > 0 ? (tune->chunk > max_chunk ? max_chunk : tune->chunk)
-                                     : (any_lo ? kDefaultChunk : max_chunk);
+                                     : (any_lo ? kDefaultChunk : (nj > 1 ? kDefaultChunkHiMulti : max_chunk));
   mp.smem = (size_t)mp.stages * mp.stage_bytes + 1024;
   return mp;
 }
