@@ -170,8 +170,10 @@ typedef struct {
 } psfsim_job_t;
 
 /* Launch-shape knobs of the tensor-core forward (0 = default): k-tiles (of 64)
- * accumulated in TMEM between drains (1..8), target work units per SM, and
- * shared-memory pipeline stages (2..8). */
+ * accumulated in TMEM between drains (at most 8 with split-BF16 storage, 16
+ * with BF16 storage: larger values are clamped), target work units per SM,
+ * and shared-memory pipeline stages (2..8; a count outside 2 .. the number
+ * that fits takes the default, as many as fit). */
 typedef struct {
   int chunk;
   int units_per_sm;
