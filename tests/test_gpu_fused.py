@@ -22,9 +22,11 @@ def _plan(lib32, radii, s, **kw):
     return Plan(torch.from_numpy(np.ascontiguousarray(lib32)).to(DEV), radii, s, **kw)
 
 
-# B = 40 and 64 run the 64-scene form of the kernel; B = 100 runs it twice (64 + 36)
+# B = 1 runs the 16-scene form with one scene; B = 33, 40 and 64 run the 64-scene form;
+# B = 65 runs it and then the 16-scene form for the last scene; B = 100 runs it twice (64 + 36)
 @pytest.mark.parametrize("n,N,S,B", [(32, 32, 0.3, 3), (24, 40, 0.2, 17), (40, 26, 0.33, 32), (16, 12, 0.5, 40),
-                                     (32, 32, 0.3, 64), (24, 20, 0.4, 100)])
+                                     (32, 32, 0.3, 64), (24, 20, 0.4, 100), (20, 18, 0.45, 1), (18, 14, 0.6, 33),
+                                     (28, 22, 0.35, 65)])
 def test_fused_forward_matches_oracle(n, N, S, B):
     rng = np.random.default_rng(n * 7 + N)
     radii = np.linspace(0.0, 4.5, 12)
