@@ -51,6 +51,39 @@ def test_split_storage_matches_oracle(n, N, S):
     assert np.array_equal(sc[: N * N], want.astype(np.float32))
 
 
+# N = 32, 64: whole 16 x 16 quadrant blocks; N = 48: whole blocks and an 8-wide edge block;
+# N = 40 (N % 16 != 0): element-by-element copies.  M = n^2 is never a multiple of 32.
+@pytest.mark.parametrize("n,N,S,storage", [(24, 32, 0.3, "split_bf16"), (20, 48, 0.2, "split_bf16"),
+                                           (36, 64, 0.12, "bf16"), (17, 40, 0.25, "split_bf16")])
+def test_symmetric_build_equals_direct_build_bit_for_bit(n, N, S, storage):
+    """An even grid is built from the x > 0, y > 0 quadrant's columns, each written to its four
+    quarter-turned positions; the same grid given as field points takes the direct build, column
+    by column.  Both must store the same bits, padding included."""
+    from paper_2106_09122_gb300 import Plan
+    from paper_2106_09122_gb300.plan import workspace_bytes
+    rng = np.random.default_rng(n * 3 + N)
+    radii = np.linspace(0.0, 0.55 * N * S, 9)  # the grid's corners lie beyond the last radius
+    lib32 = rng.uniform(0.1, 1.0, (9, n, n)).astype(np.float32)
+    lib = torch.from_numpy(lib32).to(DEV)
+    iy, ix = np.divmod(np.arange(N * N), N)
+    pts = np.stack([(ix - (N - 1) / 2) * S, (iy - (N - 1) / 2) * S], axis=1)
+    direct = Plan(lib, radii, 0.5, points=pts, storage=storage)
+    # the symmetric build's workspace comes from a block just filled with 0xFF, so a position
+    # it failed to write would not read as a matching zero
+    poison = torch.full((workspace_bytes(n, 9, N * N, storage),), 0xFF, dtype=torch.uint8, device=DEV)
+    del poison
+    sym = Plan(lib, radii, 0.5, N=N, S=S, storage=storage)
+    torch.cuda.synchronize()
+    assert sym.sync_status() == 0 and direct.sync_status() == 0
+    for a, b in zip(sym.A_split(), direct.A_split()):
+        if a is None:
+            assert b is None
+            continue
+        bits = torch.int16 if a.dtype == torch.bfloat16 else torch.int32
+        assert torch.equal(a.view(bits), b.view(bits))
+    assert torch.count_nonzero(sym.A_split()[0][: n * n, : N * N]).item() > 0
+
+
 @pytest.mark.parametrize("B", [1, 3, 16, 20, 85])
 def test_tensor_core_forward_small(B):
     rng = np.random.default_rng(40 + B)
