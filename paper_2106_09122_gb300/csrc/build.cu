@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(1024) angle_sort_kernel(const ColGeom *geom, i
 
 struct BuildParams {
   int n, n_r, Wp, compact;  // compact: column c of the sorted list is stored at position c
+  int N;                    // scene side of a grid build (0: field points)
   int64_t K, ld;
   const ColGeom *geom;
   const int *order;
@@ -324,6 +325,124 @@ __global__ void __launch_bounds__(512) build_fp32_kernel(const __grid_constant__
   }
 }
 
+// Dense FP32 storage of an even N x N grid through the exact quarter-turn
+// symmetry: R(ix, iy) = (N-1-iy, ix) on the scene and P(p, q) = (q, n-1-p) on
+// the image leave the fixed-point source coordinates unchanged, so column R(j)
+// holds at pixel P(i) the bits column j holds at i.  A warp builds one 32 x 32
+// pixel block of a column of the x > 0, y > 0 quadrant at a time (in shared
+// memory) and writes it to its four turned places, A[P^m(block), R^m(j)]:
+// every copy is 32 rows of 32 contiguous floats.
+constexpr int kSymBlk = 32, kSymPitch = 33;  // block side; shared pitch (transposed reads without conflicts)
+
+template <bool kSmem>
+__device__ __forceinline__ void build_block_sym(const BuildParams &P, int jq, int p0, int q0, const float *s0,
+                                                const float *s1, float *blk, int lane) {
+  const int N = P.N, n = P.n, H = N / 2;
+  const int iy = H + jq / H, ix = H + jq % H;  // quadrant entry jq
+  const int64_t j = (int64_t)iy * N + ix;
+  float *Am[4] = {P.A + j * P.ld, P.A + ((int64_t)ix * N + (N - 1 - iy)) * P.ld,
+                  P.A + ((int64_t)(N - 1 - iy) * N + (N - 1 - ix)) * P.ld, P.A + ((int64_t)(N - 1 - ix) * N + iy) * P.ld};
+  const ColGeom g = P.geom[jq];
+  __syncwarp();  // the previous block's copies have read the buffer
+  if (g.k < 0) {  // beyond the last radius: zeros
+    for (int a = 0; a < kSymBlk; ++a) blk[a * kSymPitch + lane] = 0.f;
+  } else {
+    const int64_t M = (int64_t)n * n;
+    const float *L0 = P.lib + (int64_t)g.k * M;
+    const float *L1 = L0 + M;
+    const int Wp = P.Wp;
+    auto tap = [&](int which, int r, int c) -> float {
+      if (kSmem) {
+        const float *s = which ? s1 : s0;
+        return s[(r + 1) * Wp + (c + 4)];
+      } else {
+        if (r < 0 || r >= n || c < 0 || c >= n) return 0.f;
+        return __ldg((which ? L1 : L0) + r * n + c);
+      }
+    };
+    const long long h = n - 1;
+    const long long base = h << PSFSIM_FRAC_BITS;
+    // lane: pixel column q0 + lane, down the block's 32 rows (exact steps)
+    const int q = q0 + lane;
+    long long a2 = base + g.C * (2 * q - h) + g.Sn * (2 * p0 - h);
+    long long b2 = base - g.Sn * (2 * q - h) + g.C * (2 * p0 - h);
+    for (int a = 0; a < kSymBlk; ++a) {
+      blk[a * kSymPitch + lane] = rotated_value(a2, b2, n, g.w0, g.w1, tap);
+      a2 += 2 * g.Sn;
+      b2 += 2 * g.C;
+    }
+  }
+  __syncwarp();
+  // row r of each turned block: m = 0 row p0 + r; m = 1 row q0 + r (source
+  // column r, rows reversed); m = 2 row n-1-p0-r (reversed); m = 3 row
+  // n-1-q0-r (source column r)
+  for (int r = 0; r < kSymBlk; ++r) {
+    __stcs(Am[0] + (int64_t)(p0 + r) * n + q0 + lane, blk[r * kSymPitch + lane]);
+    __stcs(Am[1] + (int64_t)(q0 + r) * n + (n - kSymBlk - p0) + lane, blk[(kSymBlk - 1 - lane) * kSymPitch + r]);
+    __stcs(Am[2] + (int64_t)(n - 1 - p0 - r) * n + (n - kSymBlk - q0) + lane,
+           blk[r * kSymPitch + (kSymBlk - 1 - lane)]);
+    __stcs(Am[3] + (int64_t)(n - 1 - q0 - r) * n + p0 + lane, blk[lane * kSymPitch + r]);
+  }
+}
+
+// As build_fp32_kernel, over the bracket-sorted list of the quadrant's
+// columns; each warp also owns a 32 x 33 float block buffer after the staged
+// pair.
+template <bool kSmem>
+__global__ void __launch_bounds__(512, 1) build_fp32_sym_kernel(const __grid_constant__ CUtensorMap map,
+                                                             const BuildParams P) {
+  extern __shared__ __align__(128) float smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int64_t begin = P.K * blockIdx.x / gridDim.x;
+  const int64_t end = P.K * (blockIdx.x + 1) / gridDim.x;
+  const int pair_floats = kSmem ? 2 * (P.n + 2) * P.Wp : 0;
+  float *s0 = smem;
+  float *s1 = smem + (P.n + 2) * P.Wp;
+  float *blk = smem + pair_floats + warp * (kSymBlk * kSymPitch);
+  const uint32_t tx_bytes = 2u * (uint32_t)((P.n + 2) * P.Wp) * 4u;
+  if (kSmem && threadIdx.x == 0) {
+    ptx::mbar_init(&mbar, 1);
+    ptx::fence_mbar_init();
+  }
+  __syncthreads();
+  int cur_k = -2;
+  uint32_t phase = 0;
+  bool failed = false;
+  for (int64_t pos = begin; pos < end;) {
+    const int j0 = P.order[pos];
+    const int k = P.geom[j0].k;
+    const int group_end = k < 0 ? psfsim_num_buckets(P.n_r) : (k + 1) * PSFSIM_THETA_BINS;
+    const int64_t gend = min(end, (int64_t)P.bstart[group_end]);
+    if (kSmem && k >= 0 && k != cur_k) {
+      __syncthreads();  // every warp is done with the previous pair
+      if (threadIdx.x == 0) {
+        ptx::mbar_arrive_expect_tx(&mbar, tx_bytes);
+        ptx::tma_load_3d(s0, &map, -4, -1, k, &mbar);
+      }
+      if (!ptx::mbar_wait_bounded(&mbar, phase)) failed = true;
+      cur_k = k;
+      if (__syncthreads_or(failed)) {
+        if (threadIdx.x == 0) {
+          ptx::mbar_wait_bounded(&mbar, phase);
+          atomicExch(P.status, PSFSIM_ERR_TIMEOUT);
+        }
+        return;
+      }
+      phase ^= 1u;
+    }
+    // (column, 32 x 32 pixel block) tasks of the group, dealt round-robin to
+    // the warps.
+    const int nbq = P.n / kSymBlk, nblocks = nbq * nbq;
+    for (int64_t t = warp; t < (gend - pos) * nblocks; t += nwarps) {
+      const int jq = P.order[pos + t / nblocks];
+      const int b = (int)(t % nblocks);
+      build_block_sym<kSmem>(P, jq, (b / nbq) * kSymBlk, (b % nbq) * kSymBlk, s0, s1, blk, lane);
+    }
+    pos = gend;
+  }
+}
+
 }  // namespace
 
 WsLayout psfsim_layout(int n, int64_t K, int storage, int n_r) {
@@ -390,15 +509,23 @@ static bool encode_library_map(psfsim_plan *h, int Wp) {
 }
 
 cudaError_t psfsim_launch_build(psfsim_plan *h, cudaStream_t st) {
+  // Dense storage of an even grid is built from the x > 0, y > 0 quadrant's
+  // columns, four quarter-turned copies each, so the geometry tables cover
+  // the quadrant only (entry (iy - N/2) (N/2) + ix - N/2).  The split builds
+  // take no column order.
+  const bool dense_split = h->storage == PSFSIM_SPLIT_BF16 || h->storage == PSFSIM_BF16;
+  const bool sym = !h->quadrant && h->N > 0 && h->N % 2 == 0 &&
+                   (dense_split || (h->storage == PSFSIM_FP32 && h->n % kSymBlk == 0));
+  const int64_t Kg = sym ? h->K / 4 : h->Kg;
   GeomParams G;
   std::memset(&G, 0, sizeof(G));
   G.n_r = h->n_r;
   G.N = h->N;
   G.interp = h->interp;
-  G.K = h->Kg;
+  G.K = Kg;
   G.S = h->S;
   G.pts = h->N ? nullptr : reinterpret_cast<const double *>(h->ws + h->pts_off);
-  G.quadrant = h->quadrant ? 1 : 0;
+  G.quadrant = h->quadrant || sym ? 1 : 0;
   for (int i = 0; i < h->n_r; ++i) G.radii[i] = h->radii[i];
   ColGeom *geom = reinterpret_cast<ColGeom *>(h->ws + h->geom_off);
   int *order = reinterpret_cast<int *>(h->ws + h->order_off);
@@ -406,10 +533,12 @@ cudaError_t psfsim_launch_build(psfsim_plan *h, cudaStream_t st) {
   int *status = reinterpret_cast<int *>(h->ws + h->status_off);
   cudaError_t e = cudaMemsetAsync(status, 0, 16, st);
   if (e != cudaSuccess) return e;
-  geom_kernel<<<(unsigned)((h->Kg + 255) / 256), 256, 0, st>>>(G, geom);
+  geom_kernel<<<(unsigned)((Kg + 255) / 256), 256, 0, st>>>(G, geom);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  bracket_sort_kernel<<<1, 1024, 0, st>>>(geom, h->Kg, h->n_r, order, bstart);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (!(sym && dense_split)) {
+    bracket_sort_kernel<<<1, 1024, 0, st>>>(geom, Kg, h->n_r, order, bstart);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   if (h->quadrant) {
     // The host needs the number of columns inside the last radius to size launches.
     int kv = 0;
@@ -442,6 +571,7 @@ cudaError_t psfsim_launch_build(psfsim_plan *h, cudaStream_t st) {
   P.n_r = h->n_r;
   P.Wp = Wp;
   P.compact = compact ? 1 : 0;
+  P.N = h->N;
   P.K = compact ? h->K_valid : h->K;
   P.ld = h->ld;
   P.geom = geom;
@@ -453,6 +583,21 @@ cudaError_t psfsim_launch_build(psfsim_plan *h, cudaStream_t st) {
   CUtensorMap dummy;
   std::memset(&dummy, 0, sizeof(dummy));
   int threads = 512, per_sm = 1;
+  if (sym) {
+    // Even grid: the quadrant's columns (the sorted list holds just those),
+    // four turned copies each.
+    P.K = Kg;
+    const size_t blk_bytes = 16ull * kSymBlk * kSymPitch * 4;  // 16 warps
+    const bool staged = use_smem && smem + blk_bytes <= 220 * 1024;
+    const size_t total = (staged ? smem : 0) + blk_bytes;
+    auto kern = staged ? build_fp32_sym_kernel<true> : build_fp32_sym_kernel<false>;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total)) != cudaSuccess)
+      return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, total)) != cudaSuccess) return e;
+    per_sm = per_sm < 1 ? 1 : per_sm;
+    kern<<<h->num_sms * per_sm, 512, total, st>>>(staged ? h->lib_map : dummy, P);
+    return cudaGetLastError();
+  }
   if (use_smem) {
     threads = smem > 100 * 1024 ? 512 : 256;
     auto kern = build_fp32_kernel<true, true>;

@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(256, 4) split_sym_build_kernel(const SymSplitP
       gm.w0 = gm.w1 = 0.f;
       const int ix = bx + cu, iy = by + cv;
       const bool valid = cu < bw && cv < bh;
-      if (valid) gm = P.geom[(int64_t)iy * N + ix];
+      if (valid) gm = P.geom[(int64_t)(iy - P.H) * P.H + (ix - P.H)];  // quadrant entry
       float inv = 1.f, sigma = 1.f;
       const float *L0 = P.lib, *L1 = P.lib;
       if (gm.k >= 0) {

@@ -110,6 +110,32 @@ def test_scene_grid_quarter_turn_is_bitwise():
             assert np.array_equal(b, np.rot90(a, -1))
 
 
+# n = 32, 96, 128: the bracket pair staged in shared memory; n = 192: taps read through L1/L2
+@pytest.mark.parametrize("n,N,S", [(32, 24, 0.3), (96, 20, 0.3), (128, 16, 0.5), (192, 12, 0.6)])
+def test_symmetric_build_equals_direct_build_bit_for_bit(n, N, S):
+    """An even grid with n % 32 == 0 is built from the x > 0, y > 0 quadrant's columns, each
+    written in 32 x 32 pixel blocks to its four quarter-turned places; the same grid given as
+    field points takes the direct build, column by column.  Both must store the same bits."""
+    from paper_2106_09122_gb300 import Plan
+    from paper_2106_09122_gb300.plan import workspace_bytes
+    rng = np.random.default_rng(n + 7 * N)
+    radii = np.linspace(0.0, 0.55 * N * S, 9)  # the grid's corners lie beyond the last radius
+    lib32 = rng.uniform(0.1, 1.0, (9, n, n)).astype(np.float32)
+    lib = torch.from_numpy(lib32).to(DEV)
+    iy, ix = np.divmod(np.arange(N * N), N)
+    pts = np.stack([(ix - (N - 1) / 2) * S, (iy - (N - 1) / 2) * S], axis=1)
+    direct = Plan(lib, radii, 0.5, points=pts)
+    # the symmetric build's workspace comes from a block just filled with 0xFF, so a position
+    # it failed to write would not read as a matching zero
+    poison = torch.full((workspace_bytes(n, 9, N * N, "fp32"),), 0xFF, dtype=torch.uint8, device=DEV)
+    del poison
+    sym = Plan(lib, radii, 0.5, N=N, S=S)
+    torch.cuda.synchronize()
+    assert sym.sync_status() == 0 and direct.sync_status() == 0
+    assert torch.equal(sym.A_fp32().view(torch.int32), direct.A_fp32().view(torch.int32))
+    assert torch.count_nonzero(sym.A_fp32()).item() > 0
+
+
 def test_forward_is_deterministic_and_linear_batch():
     w = workloads.plain_small()
     lib32 = w.library().astype(np.float32)
