@@ -1143,6 +1143,22 @@ def _profile_case(name: str) -> None:
         x = torch.from_numpy(ring.ravel()).to(dev)
         for _ in range(3):
             plan.forward(x, skip_zeros=True)
+    elif name == "builds":
+        # each build of A twice: the even grid (quadrant generated, four turned copies) and the
+        # same grid given as field points (the direct, column-by-column build)
+        for wname, storage in (("adjoint_128", "fp32"), ("ipac_shape", "fp32"), ("batched_256", "split_bf16")):
+            w = getattr(workloads, wname)()
+            lib = torch.from_numpy((w.library(0) if wname == "batched_256" else w.library()).astype(np.float32)).to(dev)
+            iy, ix = np.divmod(np.arange(w.N * w.N), w.N)
+            pts = np.stack([(ix - (w.N - 1) / 2) * w.S, (iy - (w.N - 1) / 2) * w.S], axis=1)
+            for grid in (True, False):
+                plan = None
+                torch.cuda.empty_cache()
+                plan = (Plan(lib, w.radii, w.s, N=w.N, S=w.S, storage=storage) if grid
+                        else Plan(lib, w.radii, w.s, points=pts, storage=storage))
+                torch.cuda.synchronize()
+                if plan.sync_status() != 0:
+                    raise SystemExit(f"build {wname} status {plan.sync_status()}")
     elif name == "sym128":
         from paper_2106_09122_gb300.fit import RingProblem
         w = workloads.adjoint_128()
@@ -1176,7 +1192,7 @@ def main():
     ap.add_argument("--main-only", action="store_true", help="skip the other workloads' measurements")
     ap.add_argument("--case", default=None,
                     help="run one small profiling case (fp32_128, fit128, sym128, sparse128, splitsym128, tc128, "
-                         "bf16_128, fused512)")
+                         "bf16_128, fused512, builds)")
     args = ap.parse_args()
     if args.case:
         _profile_case(args.case)
