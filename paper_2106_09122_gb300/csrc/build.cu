@@ -81,42 +81,68 @@ __device__ __forceinline__ int column_bucket(const ColGeom &g, int n_r) {
 
 // Stable counting sort of the columns by (radial bracket, angle bin), zero
 // columns last, so that a CTA can stage one bracket pair for many columns and
-// neighbouring columns read nearby library pixels.  The scatter is done by
-// one warp in index order (match_any ranks), so the order is deterministic.
-__global__ void __launch_bounds__(1024) bracket_sort_kernel(const ColGeom *geom, int64_t K, int n_r,
+// neighbouring columns read nearby library pixels.  One CTA; warp w of W takes
+// the w-th contiguous chunk of the columns, with its own row of bucket
+// counters in shared memory (W x buckets ints): the chunks are counted, every
+// bucket's cursor for chunk w starts after the bucket's earlier buckets and
+// the bucket's entries of chunks < w, and each warp scatters its chunk in
+// index order with match_any ranks.  The order is deterministic: by bucket,
+// ties by column index.
+__global__ void __launch_bounds__(1024) bracket_sort_kernel(const ColGeom *geom, int64_t K, int n_r, int W,
                                                             int *order, int *bstart) {
-  constexpr int kMaxBuckets = (PSFSIM_MAX_RADII - 1) * PSFSIM_THETA_BINS + 1;
-  __shared__ int cnt[kMaxBuckets];
+  extern __shared__ int cnt[];  // [W][nb]
   const int nb = psfsim_num_buckets(n_r);
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) cnt[b] = 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < W * nb; i += blockDim.x) cnt[i] = 0;
   __syncthreads();
-  for (int64_t j = threadIdx.x; j < K; j += blockDim.x) atomicAdd(&cnt[column_bucket(geom[j], n_r)], 1);
+  const int64_t c0 = K * warp / W, c1 = K * (warp + 1) / W;
+  if (warp < W)
+    for (int64_t j = c0 + lane; j < c1; j += 32) atomicAdd(&cnt[warp * nb + column_bucket(geom[j], n_r)], 1);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int run = 0;
-    for (int b = 0; b < nb; ++b) {
-      const int c = cnt[b];
-      bstart[b] = run;
-      cnt[b] = run;  // becomes the scatter cursor
-      run += c;
+  // Per bucket: its total, then the cursors of the chunks within it.
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    int t = 0;
+    for (int w = 0; w < W; ++w) {
+      const int c = cnt[w * nb + b];
+      cnt[w * nb + b] = t;
+      t += c;
     }
-    bstart[nb] = run;
+    bstart[b] = t;  // total for now
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
+  // Bucket starts: exclusive prefix of the totals, in bucket order (one warp).
+  if (warp == 0) {
+    int run = 0;
+    for (int b0 = 0; b0 < nb; b0 += 32) {
+      const int b = b0 + lane;
+      const int v = b < nb ? bstart[b] : 0;
+      int x = v;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (b < nb) bstart[b] = run + x - v;
+      run += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (lane == 0) bstart[nb] = run;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < W * nb; i += blockDim.x) cnt[i] += bstart[i % nb];
+  __syncthreads();
+  if (warp < W) {
+    int *cur = cnt + warp * nb;
     const unsigned lt = (1u << lane) - 1u;
-    for (int64_t base = 0; base < K; base += 32) {
+    for (int64_t base = c0; base < c1; base += 32) {
       const int64_t j = base + lane;
-      const int key = j < K ? column_bucket(geom[j], n_r) : -1;
+      const int key = j < c1 ? column_bucket(geom[j], n_r) : -1;
       const unsigned peers = __match_any_sync(0xffffffffu, key);
       const int leader = __ffs(peers) - 1;
       int pos0 = 0;
-      if (lane == leader && key >= 0) pos0 = cnt[key];
+      if (lane == leader && key >= 0) pos0 = cur[key];
       pos0 = __shfl_sync(0xffffffffu, pos0, leader);
       if (key >= 0) order[pos0 + __popc(peers & lt)] = (int)j;
       __syncwarp();
-      if (lane == leader && key >= 0) cnt[key] = pos0 + __popc(peers);
+      if (lane == leader && key >= 0) cur[key] = pos0 + __popc(peers);
       __syncwarp();
     }
   }
@@ -536,7 +562,17 @@ cudaError_t psfsim_launch_build(psfsim_plan *h, cudaStream_t st) {
   geom_kernel<<<(unsigned)((Kg + 255) / 256), 256, 0, st>>>(G, geom);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (!(sym && dense_split)) {
-    bracket_sort_kernel<<<1, 1024, 0, st>>>(geom, Kg, h->n_r, order, bstart);
+    // chunks of at least 256 columns, and as many as fit in shared memory
+    const int nb = psfsim_num_buckets(h->n_r);
+    int W = (int)((Kg + 255) / 256);
+    const int fit = (int)((200 * 1024) / ((size_t)nb * sizeof(int)));
+    W = W < 1 ? 1 : (W > 32 ? 32 : W);
+    W = W > fit ? fit : W;
+    const size_t smem = (size_t)W * nb * sizeof(int);
+    if ((e = cudaFuncSetAttribute(bracket_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+      return e;
+    bracket_sort_kernel<<<1, 1024, smem, st>>>(geom, Kg, h->n_r, W, order, bstart);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (h->quadrant) {
