@@ -399,15 +399,27 @@ __device__ __forceinline__ void build_block_sym(const BuildParams &P, int jq, in
     }
   }
   __syncwarp();
-  // row r of each turned block: m = 0 row p0 + r; m = 1 row q0 + r (source
+  // Row r of each turned block: m = 0 row p0 + r; m = 1 row q0 + r (source
   // column r, rows reversed); m = 2 row n-1-p0-r (reversed); m = 3 row
-  // n-1-q0-r (source column r)
-  for (int r = 0; r < kSymBlk; ++r) {
-    __stcs(Am[0] + (int64_t)(p0 + r) * n + q0 + lane, blk[r * kSymPitch + lane]);
-    __stcs(Am[1] + (int64_t)(q0 + r) * n + (n - kSymBlk - p0) + lane, blk[(kSymBlk - 1 - lane) * kSymPitch + r]);
-    __stcs(Am[2] + (int64_t)(n - 1 - p0 - r) * n + (n - kSymBlk - q0) + lane,
-           blk[r * kSymPitch + (kSymBlk - 1 - lane)]);
-    __stcs(Am[3] + (int64_t)(n - 1 - q0 - r) * n + p0 + lane, blk[lane * kSymPitch + r]);
+  // n-1-q0-r (source column r).  Lane l writes floats 4 (l % 8) .. +3 of row
+  // r0 + l / 8, so one 16-byte store instruction covers four rows (the rows
+  // are 128-byte aligned: n, p0 and q0 are multiples of 32).
+  const int rr = lane >> 3, f = (lane & 7) * 4;
+  for (int r0 = 0; r0 < kSymBlk; r0 += 4) {
+    const int r = r0 + rr;
+    float4 v0, v1, v2, v3;
+    float *a0 = &v0.x, *a1 = &v1.x, *a2 = &v2.x, *a3 = &v3.x;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      a0[i] = blk[r * kSymPitch + f + i];
+      a1[i] = blk[(kSymBlk - 1 - f - i) * kSymPitch + r];
+      a2[i] = blk[r * kSymPitch + (kSymBlk - 1 - f - i)];
+      a3[i] = blk[(f + i) * kSymPitch + r];
+    }
+    __stcs(reinterpret_cast<float4 *>(Am[0] + (int64_t)(p0 + r) * n + q0 + f), v0);
+    __stcs(reinterpret_cast<float4 *>(Am[1] + (int64_t)(q0 + r) * n + (n - kSymBlk - p0) + f), v1);
+    __stcs(reinterpret_cast<float4 *>(Am[2] + (int64_t)(n - 1 - p0 - r) * n + (n - kSymBlk - q0) + f), v2);
+    __stcs(reinterpret_cast<float4 *>(Am[3] + (int64_t)(n - 1 - q0 - r) * n + p0 + f), v3);
   }
 }
 
