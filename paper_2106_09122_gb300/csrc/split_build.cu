@@ -192,7 +192,7 @@ __device__ __forceinline__ int64_t turn_pixel(int m, int p, int q, int n) {
   return (int64_t)pp * n + qq;
 }
 
-__global__ void __launch_bounds__(256, 4) split_sym_build_kernel(const SymSplitParams P) {
+__global__ void __launch_bounds__(256, 3) split_sym_build_kernel(const SymSplitParams P) {
   __shared__ __align__(16) __nv_bfloat16 thi[kQPix][kQPitch];
   __shared__ __align__(16) __nv_bfloat16 tlo[kQPix][kQPitch];
   const int n = P.n, N = P.N;
