@@ -296,59 +296,72 @@ __device__ __forceinline__ void build_column(const BuildParams &P, int j, int64_
   for (int64_t i = M + lane; i < P.ld; i += 32) col[i] = 0.f;
 }
 
-// Each CTA owns a contiguous range of the bracket-sorted column list; when the
-// bracket changes it stages L[k], L[k+1] (zero-padded by one pixel) in shared
-// memory with one TMA tensor load, then its warps build the columns.
-template <bool kSmem, bool kVec4>
-__global__ void __launch_bounds__(512) build_fp32_kernel(const __grid_constant__ CUtensorMap map,
-                                                         const BuildParams P) {
-  extern __shared__ __align__(128) float smem[];
-  __shared__ __align__(8) uint64_t mbar;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+// Walks this CTA's contiguous range of the bracket-sorted column list group
+// by group (one radial bracket, every angle bin; or the zero columns).  With
+// kSmem, a group's bracket pair L[k], L[k+1] (zero-padded by one pixel) is
+// staged in shared memory at s0 by one TMA tensor load whenever the bracket
+// changes; then work(pos, gend) runs for the group's list positions.  The
+// whole CTA calls it (it synchronizes); mbar must be initialised.  A staging
+// copy that times out sets PSFSIM_ERR_TIMEOUT and ends the walk.
+template <bool kSmem, class GroupWork>
+__device__ __forceinline__ void for_each_bracket_group(const CUtensorMap *map, const BuildParams &P, float *s0,
+                                                       uint64_t *mbar, GroupWork work) {
   const int64_t begin = P.K * blockIdx.x / gridDim.x;
   const int64_t end = P.K * (blockIdx.x + 1) / gridDim.x;
-  float *s0 = smem;
-  float *s1 = smem + (P.n + 2) * P.Wp;
   const uint32_t tx_bytes = 2u * (uint32_t)((P.n + 2) * P.Wp) * 4u;
-  if (kSmem && threadIdx.x == 0) {
-    ptx::mbar_init(&mbar, 1);
-    ptx::fence_mbar_init();
-  }
-  __syncthreads();
   int cur_k = -2;
   uint32_t phase = 0;
   bool failed = false;
   for (int64_t pos = begin; pos < end;) {
     const int j0 = P.order[pos];
     const int k = P.geom[j0].k;
-    // All columns of one radial bracket (every angle bin) share the staged pair.
     const int group_end = k < 0 ? psfsim_num_buckets(P.n_r) : (k + 1) * PSFSIM_THETA_BINS;
     const int64_t gend = min(end, (int64_t)P.bstart[group_end]);
     if (kSmem && k >= 0 && k != cur_k) {
       __syncthreads();  // every warp is done with the previous pair
       if (threadIdx.x == 0) {
-        ptx::mbar_arrive_expect_tx(&mbar, tx_bytes);
-        ptx::tma_load_3d(s0, &map, -4, -1, k, &mbar);
+        ptx::mbar_arrive_expect_tx(mbar, tx_bytes);
+        ptx::tma_load_3d(s0, map, -4, -1, k, mbar);
       }
-      if (!ptx::mbar_wait_bounded(&mbar, phase)) failed = true;
+      if (!ptx::mbar_wait_bounded(mbar, phase)) failed = true;
       cur_k = k;
       if (__syncthreads_or(failed)) {
         // The copy may still be landing in shared memory: give it one more
         // bounded wait before the CTA exits.
         if (threadIdx.x == 0) {
-          ptx::mbar_wait_bounded(&mbar, phase);
+          ptx::mbar_wait_bounded(mbar, phase);
           atomicExch(P.status, PSFSIM_ERR_TIMEOUT);
         }
         return;
       }
       phase ^= 1u;
     }
+    work(pos, gend);
+    pos = gend;
+  }
+}
+
+// Each CTA owns a contiguous range of the bracket-sorted column list; its warps
+// build whole columns, one warp per column.
+template <bool kSmem, bool kVec4>
+__global__ void __launch_bounds__(512) build_fp32_kernel(const __grid_constant__ CUtensorMap map,
+                                                         const BuildParams P) {
+  extern __shared__ __align__(128) float smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  float *s0 = smem;
+  float *s1 = smem + (P.n + 2) * P.Wp;
+  if (kSmem && threadIdx.x == 0) {
+    ptx::mbar_init(&mbar, 1);
+    ptx::fence_mbar_init();
+  }
+  __syncthreads();
+  for_each_bracket_group<kSmem>(&map, P, s0, &mbar, [&](int64_t pos, int64_t gend) {
     for (int64_t c = pos + warp; c < gend; c += nwarps) {
       const int j = P.order[c];
       build_column<kSmem, kVec4>(P, j, P.compact ? c : (int64_t)j, s0, s1, lane);
     }
-    pos = gend;
-  }
+  });
 }
 
 // Dense FP32 storage of an even N x N grid through the exact quarter-turn
@@ -424,61 +437,32 @@ __device__ __forceinline__ void build_block_sym(const BuildParams &P, int jq, in
 }
 
 // As build_fp32_kernel, over the bracket-sorted list of the quadrant's
-// columns; each warp also owns a 32 x 33 float block buffer after the staged
-// pair.
+// columns, in (column, 32 x 32 pixel block) tasks; each warp also owns a
+// 32 x 33 float block buffer after the staged pair.
 template <bool kSmem>
 __global__ void __launch_bounds__(512, 1) build_fp32_sym_kernel(const __grid_constant__ CUtensorMap map,
                                                              const BuildParams P) {
   extern __shared__ __align__(128) float smem[];
   __shared__ __align__(8) uint64_t mbar;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  const int64_t begin = P.K * blockIdx.x / gridDim.x;
-  const int64_t end = P.K * (blockIdx.x + 1) / gridDim.x;
   const int pair_floats = kSmem ? 2 * (P.n + 2) * P.Wp : 0;
   float *s0 = smem;
   float *s1 = smem + (P.n + 2) * P.Wp;
   float *blk = smem + pair_floats + warp * (kSymBlk * kSymPitch);
-  const uint32_t tx_bytes = 2u * (uint32_t)((P.n + 2) * P.Wp) * 4u;
   if (kSmem && threadIdx.x == 0) {
     ptx::mbar_init(&mbar, 1);
     ptx::fence_mbar_init();
   }
   __syncthreads();
-  int cur_k = -2;
-  uint32_t phase = 0;
-  bool failed = false;
-  for (int64_t pos = begin; pos < end;) {
-    const int j0 = P.order[pos];
-    const int k = P.geom[j0].k;
-    const int group_end = k < 0 ? psfsim_num_buckets(P.n_r) : (k + 1) * PSFSIM_THETA_BINS;
-    const int64_t gend = min(end, (int64_t)P.bstart[group_end]);
-    if (kSmem && k >= 0 && k != cur_k) {
-      __syncthreads();  // every warp is done with the previous pair
-      if (threadIdx.x == 0) {
-        ptx::mbar_arrive_expect_tx(&mbar, tx_bytes);
-        ptx::tma_load_3d(s0, &map, -4, -1, k, &mbar);
-      }
-      if (!ptx::mbar_wait_bounded(&mbar, phase)) failed = true;
-      cur_k = k;
-      if (__syncthreads_or(failed)) {
-        if (threadIdx.x == 0) {
-          ptx::mbar_wait_bounded(&mbar, phase);
-          atomicExch(P.status, PSFSIM_ERR_TIMEOUT);
-        }
-        return;
-      }
-      phase ^= 1u;
-    }
-    // (column, 32 x 32 pixel block) tasks of the group, dealt round-robin to
-    // the warps.
-    const int nbq = P.n / kSymBlk, nblocks = nbq * nbq;
+  const int nbq = P.n / kSymBlk, nblocks = nbq * nbq;
+  for_each_bracket_group<kSmem>(&map, P, s0, &mbar, [&](int64_t pos, int64_t gend) {
+    // the group's tasks, dealt round-robin to the warps
     for (int64_t t = warp; t < (gend - pos) * nblocks; t += nwarps) {
       const int jq = P.order[pos + t / nblocks];
       const int b = (int)(t % nblocks);
       build_block_sym<kSmem>(P, jq, (b / nbq) * kSymBlk, (b % nbq) * kSymBlk, s0, s1, blk, lane);
     }
-    pos = gend;
-  }
+  });
 }
 
 }  // namespace
